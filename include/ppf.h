@@ -1,0 +1,170 @@
+/*
+ * ppf.h -- C ABI of the GB300-native polyphase filter bank (PPF).
+ *
+ * Method: Adamek, Novotny, Armour, "The Implementation of a Real-Time
+ * Polyphase Filter" (arXiv 1411.3656).  A PPF applies a T-tap FIR filter
+ * (Section 2, Eq. 1; Algorithm 1) to each of N frequency channels of a
+ * complex sample stream and then takes an N-point DFT of every filtered
+ * spectrum (Section 2: the channels are the DFT bins; Section 3: a standard
+ * forward FFT).  Concretely, for output spectrum s, channel c and bin k:
+ *
+ *     y[s][c] = sum_{t=0}^{T-1} h[t*N + c] * x[(s+t)*N + c]
+ *     Y[s][k] = sum_{c=0}^{N-1} y[s][c] * exp(-2*pi*i*k*c/N)
+ *
+ * h[c] weights the oldest of the T input rows a spectrum reads and
+ * h[(T-1)*N + c] the newest; this is Eq. 1 with b_i = h[(T-1-i)*N + c].  The
+ * DFT is forward, unnormalised, in natural bin order (k = 0..N-1).
+ *
+ * Everything runs in hand-written sm_103a CUDA kernels.  There is no CPU
+ * fallback: without a usable GPU every compute entry point returns
+ * PPF_ERR_CUDA.
+ *
+ * Conventions shared by all entry points:
+ *   - Sizes: N is a power of two, 4 <= N <= 4096; 1 <= T <= 64.  Anything
+ *     else is PPF_ERR_UNSUPPORTED.  int8 input needs N >= 8.
+ *   - Samples: PPF_IN_C32 = float2 (I, Q) 8 bytes; PPF_IN_C16 = two IEEE
+ *     half values (I, Q) 4 bytes; PPF_IN_CI8 = two signed 8-bit integers
+ *     (I, Q) 2 bytes, used unscaled.  Output is always float2 (complex64).
+ *   - Arithmetic: FIR and FFT accumulate in FP32.  h is FP32 for C32 input
+ *     and is rounded to FP16 for C16 / CI8 input.
+ *   - Device buffers belong to the caller, must be 16-byte aligned
+ *     (PPF_ERR_MISALIGNED otherwise) and must not overlap.
+ *   - Work is enqueued on the given CUDA stream (a cudaStream_t passed as
+ *     void*; NULL is the legacy default stream) and the call returns without
+ *     waiting.  Argument errors are reported synchronously and enqueue
+ *     nothing.  Errors of earlier asynchronous work surface as PPF_ERR_CUDA.
+ *   - A plan is immutable after creation and may be used from several host
+ *     threads and streams at once.  A stream object is not thread-safe.
+ */
+#ifndef PPF_H_
+#define PPF_H_
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct ppf_plan_s* ppf_plan_t;
+typedef struct ppf_stream_s* ppf_stream_t;
+
+typedef enum {
+    PPF_OK = 0,
+    PPF_ERR_INVALID_ARG = 1,   /* null pointer, negative count, too-small capacity */
+    PPF_ERR_UNSUPPORTED = 2,   /* N, T or dtype outside the supported set */
+    PPF_ERR_MISALIGNED = 3,    /* device buffer not 16-byte aligned, or overlapping */
+    PPF_ERR_OUT_OF_MEMORY = 4, /* a device or host allocation failed */
+    PPF_ERR_CUDA = 5,          /* a CUDA runtime error (this call or earlier async work) */
+    PPF_ERR_TIMEOUT = 6,       /* a bounded device-side wait gave up */
+    PPF_ERR_BUSY = 7           /* the object is in use (e.g. close with pending work) */
+} ppf_status_t;
+
+typedef enum {
+    PPF_IN_C32 = 0,            /* float2 (I, Q) */
+    PPF_IN_C16 = 1,            /* half2 (I, Q) */
+    PPF_IN_CI8 = 2             /* int8 (I, Q) */
+} ppf_dtype_t;
+
+/* Plan flags. */
+#define PPF_FLAG_NONE 0u
+#define PPF_FLAG_FIR_ONLY 1u   /* test hook: write the FIR output y instead of Y */
+#define PPF_FLAG_GENERIC 2u    /* always use the general kernel (runtime T, any size) */
+
+/*
+ * ppf_plan_create -- build a plan for N channels and T taps (Section 2, Eq. 1).
+ *   out      [out] receives the plan handle (owned by the caller; release it
+ *            with ppf_plan_destroy).
+ *   N, T     channels (power of two, 4..4096) and taps (1..64).
+ *   h_host   host array of N*T float coefficients, h[t*N + c] = tap t of
+ *            channel c.  Copied to the device; the caller keeps ownership.
+ *   in_dtype storage type of the input samples.
+ *   flags    PPF_FLAG_* bits.
+ * Allocates device memory for the coefficients and the FFT twiddle factors
+ * (computed in FP64 on the host, stored in FP32).  Synchronises the current
+ * device.  Returns PPF_ERR_UNSUPPORTED for unsupported sizes,
+ * PPF_ERR_INVALID_ARG for null pointers, PPF_ERR_OUT_OF_MEMORY or
+ * PPF_ERR_CUDA on device failure (nothing is leaked).
+ */
+ppf_status_t ppf_plan_create(ppf_plan_t* out, int N, int T, const float* h_host,
+                             ppf_dtype_t in_dtype, unsigned flags);
+
+/* Release a plan's device memory.  The caller must ensure no work using the
+ * plan is still running.  A NULL plan is PPF_ERR_INVALID_ARG. */
+ppf_status_t ppf_plan_destroy(ppf_plan_t plan);
+
+/*
+ * ppf_execute -- the whole PPF on a device-resident batch (streaming mode,
+ * the paper's M_c, Section 3).
+ *   d_in       device input, (n_spectra + T - 1) * N samples of the plan's
+ *              dtype, one contiguous stream (sample n = r*N + c is row r,
+ *              channel c).  Read only.
+ *   d_out      device output, n_spectra * N complex64, row-major [s][k].
+ *   n_spectra  number of output spectra S >= 0 (0 enqueues nothing).
+ *   stream     cudaStream_t as void*.
+ * One launch of the fused FIR+FFT kernel: each input sample is read from
+ * device memory once and filtered spectra never leave the chip.
+ */
+ppf_status_t ppf_execute(ppf_plan_t plan, const void* d_in, void* d_out,
+                         int64_t n_spectra, void* stream);
+
+/*
+ * ppf_execute_host -- the whole PPF on host buffers (the paper's single mode,
+ * M_b, Section 3, Table 2): copies host->device, runs the fused kernel and
+ * copies the spectra back, overlapping the copies of one slice with the
+ * kernel of another.  Blocks until the result is in h_out.
+ *   h_in   host input, (n_spectra + T - 1) * N samples (pinned memory gives
+ *          full link bandwidth; pageable memory works but is slower).
+ *   h_out  host output, n_spectra * N complex64.
+ * Device staging buffers are allocated on the first call and cached in the
+ * plan (released by ppf_plan_destroy); calls on one plan are serialised.
+ */
+ppf_status_t ppf_execute_host(ppf_plan_t plan, const void* h_in, void* h_out,
+                              int64_t n_spectra, void* stream);
+
+/*
+ * ppf_stream_open -- a continuous stream on top of a plan.  The stream owns a
+ * device buffer holding the FIR history: the last (T-1)*N samples plus the
+ * fewer-than-N samples of an incomplete row (Section 2: each output needs the
+ * newest sample and T-1 past samples of its channel).
+ */
+ppf_status_t ppf_stream_open(ppf_plan_t plan, ppf_stream_t* out);
+
+/*
+ * ppf_stream_push -- feed n_samples new samples (device pointer, plan dtype,
+ * any count, not necessarily a multiple of N) and emit every spectrum whose
+ * window is now complete.  After pushes totalling L samples the stream has
+ * emitted max(0, floor(L/N) - T + 1) spectra in total, identical to
+ * ppf_execute on the concatenation of all pushes.
+ *   d_out                 device output, row-major complex64 spectra.
+ *   out_capacity_spectra  rows available in d_out; if fewer than the spectra
+ *                         this push completes, PPF_ERR_INVALID_ARG and the
+ *                         stream is unchanged.
+ *   n_spectra_out [out]   spectra written by this push.
+ * Ordered on `stream`; the history update is enqueued on the same stream.
+ */
+ppf_status_t ppf_stream_push(ppf_stream_t s, const void* d_chunk, int64_t n_samples,
+                             void* d_out, int64_t out_capacity_spectra,
+                             int64_t* n_spectra_out, void* stream);
+
+/* Total samples pushed and spectra emitted so far (either pointer may be NULL). */
+ppf_status_t ppf_stream_position(ppf_stream_t s, int64_t* samples_in, int64_t* spectra_out);
+
+/* Release the stream's device history.  Synchronises the stream's last CUDA
+ * stream first, so no pushed work is pending when the memory is freed. */
+ppf_status_t ppf_stream_close(ppf_stream_t s);
+
+/* Static, human-readable name of a status code. */
+const char* ppf_status_string(ppf_status_t status);
+
+/* Which kernel ppf_execute launches for this plan, as a static string (e.g.
+ * "fused_ring" or "generic"); NULL for a NULL plan.  For tests and reports. */
+const char* ppf_plan_kernel_name(ppf_plan_t plan);
+
+/* Kernel launches this library has issued since load (for reports). */
+int64_t ppf_launch_count(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* PPF_H_ */

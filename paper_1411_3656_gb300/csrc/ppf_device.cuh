@@ -1,0 +1,222 @@
+// Device building blocks of the fused polyphase filter bank (arXiv 1411.3656).
+//
+//  * complex helpers and the in-register forward DFT of R = 2..16 points;
+//  * input decoders for complex64 / half2 / int8 I-Q storage;
+//  * one Stockham autosort pass over rows held in shared memory.
+//
+// The FFT is the DFT stage of the PPF (Section 2: channels are DFT bins;
+// Section 3 uses a standard forward FFT): forward sign, unnormalised, natural
+// bin order.  A length-N row is transformed by passes of radix R_1, R_2, ...
+// with N = R_1 * R_2 * ... .  Pass p has Ns = R_1 * ... * R_{p-1} (the length
+// of the sub-transforms already done).  Butterfly j (0 <= j < N/R) of the pass
+// reads elements j + r*N/R, multiplies element r by W_{Ns*R}^{(j mod Ns)*r},
+// takes an R-point DFT and writes output q to (j div Ns)*Ns*R + (j mod Ns) +
+// q*Ns.  After the last pass (Ns*R = N) the row holds the DFT in natural
+// order; no bit reversal is needed.
+#pragma once
+
+#include <cuda_fp16.h>
+#include <cstdint>
+
+namespace ppf {
+
+// ------------------------------------------------------------------ complex
+__device__ __forceinline__ float2 cadd(float2 a, float2 b) { return make_float2(a.x + b.x, a.y + b.y); }
+__device__ __forceinline__ float2 csub(float2 a, float2 b) { return make_float2(a.x - b.x, a.y - b.y); }
+__device__ __forceinline__ float2 cmul(float2 a, float2 w)
+{
+    return make_float2(fmaf(a.x, w.x, -a.y * w.y), fmaf(a.x, w.y, a.y * w.x));
+}
+// a * (-i)
+__device__ __forceinline__ float2 cmul_mi(float2 a) { return make_float2(a.y, -a.x); }
+
+// cos(pi/8), sin(pi/8), cos(pi/4): exact mathematical constants rounded to float.
+#define PPF_C8 0.92387953251128675613f
+#define PPF_S8 0.38268343236508977173f
+#define PPF_R2 0.70710678118654752440f
+
+// a * W_16^m with W_16 = exp(-2*pi*i/16); m is a compile-time constant after
+// unrolling, so the switch folds to the few instructions each case needs.
+__device__ __forceinline__ float2 mul_w16(int m, float2 a)
+{
+    m &= 15;
+    const bool neg = m >= 8;           // W^(m+8) = -W^m
+    if (neg) m -= 8;
+    float2 r;
+    switch (m) {
+    case 0: r = a; break;
+    case 1: r = make_float2(fmaf(a.x, PPF_C8, a.y * PPF_S8), fmaf(a.y, PPF_C8, -a.x * PPF_S8)); break;
+    case 2: r = make_float2((a.x + a.y) * PPF_R2, (a.y - a.x) * PPF_R2); break;
+    case 3: r = make_float2(fmaf(a.x, PPF_S8, a.y * PPF_C8), fmaf(a.y, PPF_S8, -a.x * PPF_C8)); break;
+    case 4: r = make_float2(a.y, -a.x); break;
+    case 5: r = make_float2(fmaf(-a.x, PPF_S8, a.y * PPF_C8), fmaf(-a.y, PPF_S8, -a.x * PPF_C8)); break;
+    case 6: r = make_float2((a.y - a.x) * PPF_R2, -(a.x + a.y) * PPF_R2); break;
+    default: r = make_float2(fmaf(-a.x, PPF_C8, a.y * PPF_S8), fmaf(-a.y, PPF_C8, -a.x * PPF_S8)); break;
+    }
+    return neg ? make_float2(-r.x, -r.y) : r;
+}
+
+// In-register forward DFT of R points (R = 1, 2, 4, 8, 16), natural order in
+// and out: v[k] <- sum_r v[r] * W_R^{r*k}.  Radix-2 decimation in time over
+// compile-time indices; the even/odd copies are register renames.
+template <int R>
+__device__ __forceinline__ void dft(float2 (&v)[R])
+{
+    if constexpr (R == 1) {
+        return;
+    } else if constexpr (R == 2) {
+        const float2 a = v[0], b = v[1];
+        v[0] = cadd(a, b);
+        v[1] = csub(a, b);
+    } else if constexpr (R == 4) {
+        const float2 t0 = cadd(v[0], v[2]), t1 = csub(v[0], v[2]);
+        const float2 t2 = cadd(v[1], v[3]), t3 = cmul_mi(csub(v[1], v[3]));
+        v[0] = cadd(t0, t2);
+        v[2] = csub(t0, t2);
+        v[1] = cadd(t1, t3);
+        v[3] = csub(t1, t3);
+    } else {
+        static_assert(R == 8 || R == 16, "radix must be 1, 2, 4, 8 or 16");
+        float2 e[R / 2], o[R / 2];
+#pragma unroll
+        for (int i = 0; i < R / 2; ++i) {
+            e[i] = v[2 * i];
+            o[i] = v[2 * i + 1];
+        }
+        dft<R / 2>(e);
+        dft<R / 2>(o);
+#pragma unroll
+        for (int k = 0; k < R / 2; ++k) {
+            const float2 t = mul_w16(k * (16 / R), o[k]);
+            v[k] = cadd(e[k], t);
+            v[k + R / 2] = csub(e[k], t);
+        }
+    }
+}
+
+// ------------------------------------------------------------------ inputs
+// Storage types of the input samples.
+struct InC32 { using raw = float2;  static constexpr int bytes = 8; };
+struct InC16 { using raw = __half2; static constexpr int bytes = 4; };
+struct InCI8 { using raw = char2;   static constexpr int bytes = 2; };
+
+__device__ __forceinline__ float2 decode(float2 v) { return v; }
+__device__ __forceinline__ float2 decode(__half2 v) { return __half22float2(v); }
+__device__ __forceinline__ float2 decode(char2 v) { return make_float2((float)v.x, (float)v.y); }
+
+// Two consecutive samples as one vector: 16 B (c32), 8 B (c16), 4 B (ci8).
+template <class In> struct Pair;
+template <> struct Pair<InC32> {
+    using vec = float4;
+    __device__ static void split(const vec& p, float2& a, float2& b) { a = make_float2(p.x, p.y); b = make_float2(p.z, p.w); }
+};
+template <> struct Pair<InC16> {
+    using vec = uint2;
+    __device__ static void split(const vec& p, float2& a, float2& b)
+    {
+        __half2 h0 = *reinterpret_cast<const __half2*>(&p.x);
+        __half2 h1 = *reinterpret_cast<const __half2*>(&p.y);
+        a = __half22float2(h0);
+        b = __half22float2(h1);
+    }
+};
+template <> struct Pair<InCI8> {
+    using vec = char4;
+    __device__ static void split(const vec& p, float2& a, float2& b)
+    {
+        a = make_float2((float)p.x, (float)p.y);
+        b = make_float2((float)p.z, (float)p.w);
+    }
+};
+
+// Coefficient storage: FP32 for complex64 input, FP16 for the reduced types.
+template <class In> struct Coef { using type = __half; };
+template <> struct Coef<InC32> { using type = float; };
+__device__ __forceinline__ float coef_f(float v) { return v; }
+__device__ __forceinline__ float coef_f(__half v) { return __half2float(v); }
+
+// ------------------------------------------------------------------ FFT plan
+// Radix of pass p for a length-N row: 16 first (or N itself when N <= 16),
+// then 16s, the remainder last.  Every pass after the first has Ns >= 16.
+__host__ __device__ constexpr int fft_npass(int N)
+{
+    int p = 0;
+    for (int n = N; n > 1;) {
+        const int r = n >= 16 ? 16 : n;
+        n /= r;
+        ++p;
+    }
+    return p;
+}
+__host__ __device__ constexpr int fft_radix(int N, int pass)
+{
+    int n = N;
+    for (int p = 0;; ++p) {
+        const int r = n >= 16 ? 16 : n;
+        if (p == pass) return r;
+        n /= r;
+    }
+}
+__host__ __device__ constexpr int fft_ns(int N, int pass)
+{
+    int ns = 1;
+    for (int p = 0; p < pass; ++p) ns *= fft_radix(N, p);
+    return ns;
+}
+
+// Shared-memory row stride (in float2 slots) of the FFT buffer: N plus the
+// padding of the first pass (one slot per 16 elements), at least 2 so that
+// rows stay 16-byte aligned for vector stores.
+__host__ __device__ constexpr int fft_row_stride(int N) { return N + (N / 16 > 2 ? N / 16 : 2); }
+
+// Physical slot of logical element idx in a buffer written by a pass with
+// parameters (NS, R).  With NS < 16 the writes of a half-warp would collide
+// in the 16 eight-byte bank slots; padding NS slots after every NS*R
+// elements spreads them over distinct slots while the next pass's reads (16
+// consecutive elements from a 16-aligned start) stay contiguous.
+template <int NS, int R>
+__device__ __forceinline__ int pad_slot(int idx)
+{
+    if constexpr (NS >= 16 || NS * R < 2) return idx;
+    else return idx + NS * (idx / (NS * R));
+}
+
+// Load the R inputs of butterfly j of a pass from row `row` of `buf`.
+// InNS/InR describe the pass that wrote the buffer (InNS == 0: unpadded).
+template <int N, int R, int InNS, int InR>
+__device__ __forceinline__ void pass_load(const float2* buf, int row, int j, float2 (&v)[R])
+{
+    constexpr int RS = fft_row_stride(N);
+    const float2* b = buf + row * RS;
+#pragma unroll
+    for (int r = 0; r < R; ++r) {
+        const int idx = j + r * (N / R);
+        if constexpr (InNS == 0) v[r] = b[idx];
+        else v[r] = b[pad_slot<InNS, InR>(idx)];
+    }
+}
+
+// Twiddle W_{NS*R}^{(j mod NS)*r} for r = 1..R-1 from the table tw[m] = W_N^m.
+template <int N, int R, int NS>
+__device__ __forceinline__ void pass_twiddle(const float2* __restrict__ tw, int j, float2 (&v)[R])
+{
+    if constexpr (NS > 1) {
+        const int k = j % NS;
+        constexpr int step = N / (NS * R);
+#pragma unroll
+        for (int r = 1; r < R; ++r) v[r] = cmul(v[r], tw[k * r * step]);
+    }
+}
+
+// Store the R outputs of butterfly j into row `row` of `buf` (padded for NS).
+template <int N, int R, int NS>
+__device__ __forceinline__ void pass_store(float2* buf, int row, int j, const float2 (&v)[R])
+{
+    constexpr int RS = fft_row_stride(N);
+    float2* b = buf + row * RS;
+    const int base = (j / NS) * NS * R + (j % NS);
+#pragma unroll
+    for (int q = 0; q < R; ++q) b[pad_slot<NS, R>(base + q * NS)] = v[q];
+}
+
+}  // namespace ppf

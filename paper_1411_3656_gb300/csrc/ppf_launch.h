@@ -1,0 +1,35 @@
+// Host-side kernel registry shared by the translation units of libppf.so.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <cstdint>
+
+namespace ppf {
+
+// What a launcher needs to know about a plan (plain data, no ownership).
+struct PlanView {
+    int N = 0, T = 0, dtype = 0;
+    const void* h = nullptr;      // device coefficients: float (c32) or __half (c16/ci8), [T*N]
+    const float2* tw = nullptr;   // device twiddles W_N^m, m = 0..N-1
+    int sms = 0;                  // multiprocessors of the plan's device
+    int grid_cap = 0;             // resident CTAs for the chosen kernel (set by prepare)
+    int fir_only = 0;             // test hook: store y instead of Y
+};
+
+using PrepareFn = cudaError_t (*)(PlanView&);
+using LaunchFn = cudaError_t (*)(const PlanView&, const void* in, float2* out, int64_t S,
+                                 cudaStream_t stream);
+
+struct KernelEntry {
+    const char* name = nullptr;
+    PrepareFn prepare = nullptr;
+    LaunchFn launch = nullptr;
+};
+
+// General kernel for (N, dtype); runtime T.  Defined in ppf_generic.cu.
+KernelEntry generic_entry(int N, int dtype);
+
+// Counts kernel launches issued by the library.
+void note_launch();
+
+}  // namespace ppf

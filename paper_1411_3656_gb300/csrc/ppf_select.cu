@@ -1,0 +1,16 @@
+// Kernel selection for a plan: the specialised kernel for (N, T, dtype) when
+// one is compiled in, otherwise an empty entry (the plan then uses the general
+// kernel, which handles every supported size).
+#include "ppf_launch.h"
+
+namespace ppf {
+
+KernelEntry select_fast_entry(int N, int T, int dtype)
+{
+    (void)N;
+    (void)T;
+    (void)dtype;
+    return KernelEntry{};
+}
+
+}  // namespace ppf

@@ -1,0 +1,268 @@
+"""ctypes binding of libppf.so (declared in include/ppf.h).
+
+Argument marshalling only: every step of the polyphase filter bank runs in the
+library's CUDA kernels.  PyTorch supplies device memory and streams.  If the
+library is missing or cannot be loaded, every call raises; there is no CPU
+fallback.
+
+Low-level functions carry the C names (``ppf_plan_create``, ``ppf_execute``,
+``ppf_execute_host``, ``ppf_stream_open``, ``ppf_stream_push``,
+``ppf_stream_close`` ...).  ``Plan`` and ``Stream`` wrap them for torch tensors.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import threading
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libppf.so")
+
+PPF_OK = 0
+STATUS = {0: "PPF_OK", 1: "PPF_ERR_INVALID_ARG", 2: "PPF_ERR_UNSUPPORTED", 3: "PPF_ERR_MISALIGNED",
+          4: "PPF_ERR_OUT_OF_MEMORY", 5: "PPF_ERR_CUDA", 6: "PPF_ERR_TIMEOUT", 7: "PPF_ERR_BUSY"}
+DTYPES = {"c32": 0, "c16": 1, "ci8": 2}
+SAMPLE_BYTES = {"c32": 8, "c16": 4, "ci8": 2}
+FLAG_FIR_ONLY = 1
+FLAG_GENERIC = 2
+
+#: every entry point declared in include/ppf.h
+EXPORTS = ("ppf_plan_create", "ppf_plan_destroy", "ppf_execute", "ppf_execute_host",
+           "ppf_stream_open", "ppf_stream_push", "ppf_stream_position", "ppf_stream_close",
+           "ppf_status_string", "ppf_plan_kernel_name", "ppf_launch_count")
+
+
+class PPFError(RuntimeError):
+    def __init__(self, status: int, where: str):
+        super().__init__(f"{where}: {STATUS.get(status, status)}")
+        self.status = status
+
+
+_lock = threading.Lock()
+_lib = None
+
+
+def load(path: str | None = None):
+    """Load libppf.so and declare its signatures (no GPU needed for loading)."""
+    global _lib
+    with _lock:
+        if _lib is not None and path is None:
+            return _lib
+        p = path or LIB_PATH
+        if not os.path.exists(p):
+            raise RuntimeError(f"{p} is missing: build it with paper_1411_3656_gb300.build.build()")
+        lib = ctypes.CDLL(p)
+        vp, i64, i32 = ctypes.c_void_p, ctypes.c_int64, ctypes.c_int
+        sig = {
+            "ppf_plan_create": ([ctypes.POINTER(vp), i32, i32, ctypes.POINTER(ctypes.c_float), i32,
+                                 ctypes.c_uint], i32),
+            "ppf_plan_destroy": ([vp], i32),
+            "ppf_execute": ([vp, vp, vp, i64, vp], i32),
+            "ppf_execute_host": ([vp, vp, vp, i64, vp], i32),
+            "ppf_stream_open": ([vp, ctypes.POINTER(vp)], i32),
+            "ppf_stream_push": ([vp, vp, i64, vp, i64, ctypes.POINTER(i64), vp], i32),
+            "ppf_stream_position": ([vp, ctypes.POINTER(i64), ctypes.POINTER(i64)], i32),
+            "ppf_stream_close": ([vp], i32),
+            "ppf_status_string": ([i32], ctypes.c_char_p),
+            "ppf_plan_kernel_name": ([vp], ctypes.c_char_p),
+            "ppf_launch_count": ([], i64),
+        }
+        for name, (args, res) in sig.items():
+            fn = getattr(lib, name)
+            fn.argtypes = args
+            fn.restype = res
+        if path is None:
+            _lib = lib
+        return lib
+
+
+def _check(status: int, where: str):
+    if status != PPF_OK:
+        raise PPFError(status, where)
+
+
+def _stream_ptr(stream) -> int:
+    if stream is None:
+        import torch
+        return torch.cuda.current_stream().cuda_stream
+    if isinstance(stream, int):
+        return stream
+    return stream.cuda_stream
+
+
+# -- C-named entry points ----------------------------------------------------
+
+def ppf_plan_create(N: int, T: int, h, dtype: str = "c32", flags: int = 0) -> int:
+    import numpy as np
+    hh = np.ascontiguousarray(np.asarray(h, dtype=np.float32).reshape(-1))
+    if hh.size != N * T:
+        raise ValueError("h must hold N*T coefficients")
+    out = ctypes.c_void_p()
+    st = load().ppf_plan_create(ctypes.byref(out), int(N), int(T),
+                                hh.ctypes.data_as(ctypes.POINTER(ctypes.c_float)), DTYPES[dtype], int(flags))
+    _check(st, "ppf_plan_create")
+    return out.value
+
+
+def ppf_plan_destroy(plan: int):
+    _check(load().ppf_plan_destroy(plan), "ppf_plan_destroy")
+
+
+def ppf_execute(plan: int, d_in: int, d_out: int, n_spectra: int, stream: int = 0) -> int:
+    return load().ppf_execute(plan, d_in, d_out, int(n_spectra), stream)
+
+
+def ppf_execute_host(plan: int, h_in: int, h_out: int, n_spectra: int, stream: int = 0) -> int:
+    return load().ppf_execute_host(plan, h_in, h_out, int(n_spectra), stream)
+
+
+def ppf_stream_open(plan: int) -> int:
+    out = ctypes.c_void_p()
+    _check(load().ppf_stream_open(plan, ctypes.byref(out)), "ppf_stream_open")
+    return out.value
+
+
+def ppf_stream_push(stream_obj: int, d_chunk: int, n_samples: int, d_out: int, capacity: int,
+                    cuda_stream: int = 0):
+    n = ctypes.c_int64(0)
+    st = load().ppf_stream_push(stream_obj, d_chunk, int(n_samples), d_out, int(capacity),
+                                ctypes.byref(n), cuda_stream)
+    return st, n.value
+
+
+def ppf_stream_position(stream_obj: int):
+    a, b = ctypes.c_int64(0), ctypes.c_int64(0)
+    _check(load().ppf_stream_position(stream_obj, ctypes.byref(a), ctypes.byref(b)), "ppf_stream_position")
+    return a.value, b.value
+
+
+def ppf_stream_close(stream_obj: int):
+    _check(load().ppf_stream_close(stream_obj), "ppf_stream_close")
+
+
+def ppf_status_string(status: int) -> str:
+    return load().ppf_status_string(int(status)).decode()
+
+
+def ppf_plan_kernel_name(plan: int) -> str:
+    r = load().ppf_plan_kernel_name(plan)
+    return r.decode() if r else ""
+
+
+def ppf_launch_count() -> int:
+    return int(load().ppf_launch_count())
+
+
+# -- torch-facing wrappers -----------------------------------------------------
+
+def dtype_of(x) -> str:
+    """Storage name of a torch input tensor: complex64 -> c32; float16 [...,2] -> c16; int8 [...,2] -> ci8."""
+    import torch
+    if x.dtype == torch.complex64:
+        return "c32"
+    if x.dtype == torch.float16:
+        return "c16"
+    if x.dtype == torch.int8:
+        return "ci8"
+    raise TypeError(f"unsupported input dtype {x.dtype}")
+
+
+def n_samples_of(x) -> int:
+    import torch
+    if x.dtype == torch.complex64:
+        return x.numel()
+    return x.numel() // 2
+
+
+class Plan:
+    """A PPF plan: N channels, T taps, coefficients h[t*N + c] (float32)."""
+
+    def __init__(self, N: int, T: int, h, dtype: str = "c32", flags: int = 0):
+        self.N, self.T, self.dtype, self.flags = int(N), int(T), dtype, int(flags)
+        self.handle = ppf_plan_create(N, T, h, dtype, flags)
+
+    @property
+    def kernel(self) -> str:
+        return ppf_plan_kernel_name(self.handle)
+
+    def close(self):
+        if self.handle:
+            ppf_plan_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def n_spectra(self, x) -> int:
+        return max(0, n_samples_of(x) // self.N - self.T + 1)
+
+    def execute(self, x, out=None, n_spectra: int | None = None, stream=None):
+        """Run the PPF on device tensor ``x``; returns complex64 [n_spectra, N]."""
+        import torch
+        if dtype_of(x) != self.dtype:
+            raise TypeError(f"plan expects {self.dtype} input, got {dtype_of(x)}")
+        if not x.is_cuda or not x.is_contiguous():
+            raise ValueError("input must be a contiguous CUDA tensor")
+        S = self.n_spectra(x) if n_spectra is None else int(n_spectra)
+        if n_samples_of(x) < (S + self.T - 1) * self.N and S > 0:
+            raise ValueError("input too short for n_spectra")
+        if out is None:
+            out = torch.empty((S, self.N), dtype=torch.complex64, device=x.device)
+        elif out.numel() < S * self.N or out.dtype != torch.complex64 or not out.is_contiguous():
+            raise ValueError("out must be a contiguous complex64 tensor of at least n_spectra*N")
+        st = ppf_execute(self.handle, x.data_ptr(), out.data_ptr(), S, _stream_ptr(stream))
+        _check(st, "ppf_execute")
+        return out
+
+    __call__ = execute
+
+    def execute_host(self, x_host, out_host=None, n_spectra: int | None = None, stream=None):
+        """Host-buffer PPF (copies inside).  ``x_host`` is a CPU tensor (pinned for speed)."""
+        import torch
+        S = self.n_spectra(x_host) if n_spectra is None else int(n_spectra)
+        if out_host is None:
+            out_host = torch.empty((S, self.N), dtype=torch.complex64, pin_memory=x_host.is_pinned())
+        st = ppf_execute_host(self.handle, x_host.data_ptr(), out_host.data_ptr(), S, _stream_ptr(stream))
+        _check(st, "ppf_execute_host")
+        return out_host
+
+
+class Stream:
+    """Continuous stream on a plan; push chunks, receive completed spectra."""
+
+    def __init__(self, plan: Plan):
+        self.plan = plan
+        self.handle = ppf_stream_open(plan.handle)
+
+    def push(self, chunk, out=None, stream=None):
+        import torch
+        n = n_samples_of(chunk) if chunk is not None else 0
+        pushed, emitted = ppf_stream_position(self.handle)
+        total = pushed + n
+        fresh = max(0, total // self.plan.N - self.plan.T + 1) - emitted
+        if out is None:
+            dev = chunk.device if chunk is not None else torch.device("cuda")
+            out = torch.empty((max(fresh, 0), self.plan.N), dtype=torch.complex64, device=dev)
+        cap = out.numel() // self.plan.N
+        st, got = ppf_stream_push(self.handle, chunk.data_ptr() if n else 0, n,
+                                  out.data_ptr() if out.numel() else 0, cap, _stream_ptr(stream))
+        _check(st, "ppf_stream_push")
+        return out[:got]
+
+    @property
+    def position(self):
+        return ppf_stream_position(self.handle)
+
+    def close(self):
+        if self.handle:
+            ppf_stream_close(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

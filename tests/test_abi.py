@@ -1,0 +1,60 @@
+"""The C-ABI library loads and exports every entry point include/ppf.h declares (no GPU needed)."""
+import os
+import re
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def _declared():
+    names = set()
+    for fn in os.listdir(os.path.join(ROOT, "include")):
+        if fn.endswith(".h"):
+            src = open(os.path.join(ROOT, "include", fn)).read()
+            src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+            names |= set(re.findall(r"^[A-Za-z_][\w\s\*]*?\b(ppf_\w+)\s*\(", src, flags=re.M))
+    return names
+
+
+@pytest.fixture(scope="module")
+def lib():
+    from paper_1411_3656_gb300 import build, ppf
+    build.build()
+    return ppf.load()
+
+
+def test_header_declares_entry_points():
+    from paper_1411_3656_gb300 import ppf
+    assert _declared() == set(ppf.EXPORTS)
+
+
+def test_library_exports_every_declared_symbol(lib):
+    for name in _declared():
+        assert hasattr(lib, name), name
+
+
+def test_status_strings(lib):
+    from paper_1411_3656_gb300 import ppf
+    for code, name in ppf.STATUS.items():
+        assert ppf.ppf_status_string(code) == name
+
+
+def test_unsupported_sizes_rejected_before_any_device_call(lib):
+    import ctypes
+    import numpy as np
+    from paper_1411_3656_gb300 import ppf
+    h = np.ones(4096 * 64, dtype=np.float32)
+    hp = h.ctypes.data_as(ctypes.POINTER(ctypes.c_float))
+    out = ctypes.c_void_p()
+    for N, T, dt in [(3, 4, 0), (6, 4, 0), (8192, 4, 0), (2, 4, 0), (256, 0, 0), (256, 65, 0),
+                     (4, 4, 2), (256, 8, 7)]:
+        assert lib.ppf_plan_create(ctypes.byref(out), N, T, hp, dt, 0) == 2, (N, T, dt)
+    assert lib.ppf_plan_create(None, 256, 8, hp, 0, 0) == 1
+    assert lib.ppf_plan_create(ctypes.byref(out), 256, 8, None, 0, 0) == 1
+    assert lib.ppf_plan_destroy(None) == 1
+    assert lib.ppf_execute(None, None, None, 1, None) == 1
+    assert lib.ppf_stream_push(None, None, 0, None, 0, None, None) == 1
+    assert lib.ppf_stream_close(None) == 1
+    assert lib.ppf_plan_kernel_name(None) is None
+    assert ppf.ppf_launch_count() >= 0

@@ -1,0 +1,205 @@
+"""GPU parity: the CUDA path through the C ABI against the FP64 oracle.
+
+Tolerances (relative L2 over the compared spectra, FP64):
+  * complex64 input, FP32 arithmetic: <= 1e-5;
+  * float16 / int8 storage against the oracle on the stored values with the
+    caller's FP32 h: <= 3e-3 (covers the FP16 rounding of h), and <= 1e-5
+    against the oracle run with the FP16-rounded h the device uses.
+"""
+import numpy as np
+import pytest
+
+import oracle
+from paper_1411_3656_gb300 import synth
+
+pytestmark = pytest.mark.gpu
+
+TOL32 = 1e-5
+TOL_REDUCED = 3e-3
+
+
+@pytest.fixture(scope="module")
+def ppf():
+    import torch
+    from paper_1411_3656_gb300 import build, ppf as mod
+    build.build()
+    mod.load()
+    assert torch.cuda.is_available()
+    return mod
+
+
+def _dev(a):
+    import torch
+    return torch.from_numpy(np.ascontiguousarray(a)).to("cuda")
+
+
+def _run(ppf, x, h, N, T, S, dtype="c32", flags=0):
+    import torch
+    plan = ppf.Plan(N, T, h, dtype, flags)
+    xd = _dev(x)
+    before = ppf.ppf_launch_count()
+    Y = plan(xd, n_spectra=S)
+    torch.cuda.synchronize()
+    if S > 0:
+        assert ppf.ppf_launch_count() > before
+    return Y.cpu().numpy(), plan.kernel
+
+
+def _rand(N, T, S, seed):
+    x = synth.stream(synth.samples_for(S, N, T), N, seed)
+    g = np.random.default_rng(seed)
+    h = g.standard_normal(N * T).astype(np.float32)
+    return x, h
+
+
+def test_plain_config_n256_t8_s1024(ppf):
+    """N=256, T=8, 1024 spectra, Hamming-sinc h, noise + 3 tones: the whole output."""
+    x, h, N, T, S = synth.plain_config()
+    Y, kern = _run(ppf, x, h, N, T, S)
+    ref = oracle.ppf(x, h, N, T, S)
+    err = synth.rel_l2(Y, ref)
+    assert err <= TOL32, (kern, err)
+
+
+SIZES = [(4, 1, 37), (4, 3, 50), (8, 2, 41), (16, 4, 33), (32, 5, 70), (64, 8, 39), (128, 4, 77),
+         (256, 8, 45), (256, 1, 19), (512, 16, 21), (1024, 8, 19), (1024, 32, 9), (2048, 4, 11),
+         (4096, 8, 7), (4096, 32, 5), (256, 64, 13), (128, 13, 29)]
+
+
+@pytest.mark.parametrize("N,T,S", SIZES)
+@pytest.mark.parametrize("generic", [False, True])
+def test_sizes_ragged(ppf, N, T, S, generic):
+    x, h = _rand(N, T, S, 1000 + N + 7 * T)
+    Y, kern = _run(ppf, x, h, N, T, S, flags=ppf.FLAG_GENERIC if generic else 0)
+    if generic:
+        assert kern == "generic"
+    ref = oracle.ppf(x, h, N, T, S)
+    assert synth.rel_l2(Y, ref) <= TOL32, kern
+
+
+@pytest.mark.parametrize("N,T,S", [(16, 3, 9), (256, 8, 31), (4096, 4, 3)])
+def test_fir_only_hook(ppf, N, T, S):
+    x, h = _rand(N, T, S, 77)
+    Y, kern = _run(ppf, x, h, N, T, S, flags=ppf.FLAG_FIR_ONLY)
+    ref = oracle.fir(x, h, N, T, S)
+    assert synth.rel_l2(Y, ref) <= TOL32
+
+
+def test_impulse_on_device(ppf):
+    """Impulse reproduces h on the GPU as well (convention check independent of tolerance)."""
+    N, T, S = 64, 4, 10
+    h = np.random.default_rng(5).standard_normal(N * T).astype(np.float32)
+    x = np.zeros((S + T - 1) * N, dtype=np.complex64)
+    r, c0 = 6, 9
+    x[r * N + c0] = 1.0
+    Y, _ = _run(ppf, x, h, N, T, S)
+    k = np.arange(N)
+    for s in range(S):
+        t = r - s
+        want = h[t * N + c0] * np.exp(-2j * np.pi * k * c0 / N) if 0 <= t < T else np.zeros(N)
+        assert np.allclose(Y[s], want, atol=2e-6 * max(1.0, np.abs(h).max()))
+
+
+def test_zero_and_single_spectrum(ppf):
+    import torch
+    N, T = 256, 8
+    x, h = _rand(N, T, 1, 3)
+    plan = ppf.Plan(N, T, h)
+    xd = _dev(x)
+    before = ppf.ppf_launch_count()
+    out = torch.empty((0, N), dtype=torch.complex64, device="cuda")
+    assert ppf.ppf_execute(plan.handle, xd.data_ptr(), out.data_ptr(), 0, 0) == 0
+    assert ppf.ppf_launch_count() == before
+    Y = plan(xd, n_spectra=1)
+    torch.cuda.synchronize()
+    assert synth.rel_l2(Y.cpu().numpy(), oracle.ppf(x, h, N, T, 1)) <= TOL32
+
+
+def test_argument_errors(ppf):
+    import torch
+    N, T = 256, 8
+    h = np.ones(N * T, np.float32)
+    plan = ppf.Plan(N, T, h)
+    x = torch.zeros(N * (T + 4) + 4, dtype=torch.complex64, device="cuda")
+    y = torch.zeros(16 * N + 2, dtype=torch.complex64, device="cuda")
+    assert ppf.ppf_execute(plan.handle, x.data_ptr() + 8, y.data_ptr(), 4, 0) == 3  # misaligned in
+    assert ppf.ppf_execute(plan.handle, x.data_ptr(), y.data_ptr() + 8, 4, 0) == 3  # misaligned out
+    assert ppf.ppf_execute(plan.handle, x.data_ptr(), x.data_ptr() + 16 * N, 4, 0) == 3  # overlap
+    assert ppf.ppf_execute(plan.handle, x.data_ptr(), y.data_ptr(), -1, 0) == 1
+
+
+@pytest.mark.parametrize("dtype", ["c16", "ci8"])
+def test_reduced_precision_n1024_t8(ppf, dtype):
+    """FP16 / int8 I-Q storage at N=1024, T=8 (FP32 accumulation, FP16 h)."""
+    N, T, S = 1024, 8, 64
+    n = synth.samples_for(S, N, T)
+    if dtype == "c16":
+        xs = synth.to_fp16_iq(synth.stream(n, N, 4242))
+    else:
+        xs = synth.int8_iq(n, 4243)
+    h = synth.hamming_sinc(N, T)
+    Y, _ = _run(ppf, xs, h, N, T, S, dtype=dtype)
+    err = synth.rel_l2(Y, oracle.ppf(xs, h, N, T, S))
+    assert err <= TOL_REDUCED, err
+    h16 = h.astype(np.float16).astype(np.float32)
+    assert synth.rel_l2(Y, oracle.ppf(xs, h16, N, T, S)) <= TOL32
+
+
+@pytest.mark.parametrize("N,T", [(256, 8), (1024, 16), (64, 3)])
+def test_stream_equals_batch(ppf, N, T):
+    """Pushing chunks of arbitrary length emits exactly the batch result."""
+    import torch
+    total = N * 57 + 13
+    h = np.random.default_rng(31 + N).standard_normal(N * T).astype(np.float32)
+    x = synth.stream(total, N, 31 + N)
+    plan = ppf.Plan(N, T, h)
+    batch = plan(_dev(x)).cpu().numpy()
+    st = ppf.Stream(plan)
+    g = np.random.default_rng(8)
+    sizes = [1, N - 1, 3 * N + 5, 0, 2 * N, 7, N * 11 + 1]
+    pos, i, outs = 0, 0, []
+    while pos < total:
+        n = sizes[i] if i < len(sizes) else int(g.integers(1, 4 * N))
+        i += 1
+        n = min(n, total - pos)
+        chunk = _dev(x[pos:pos + n]) if n else None
+        outs.append(st.push(chunk).cpu().numpy())
+        pos += n
+    torch.cuda.synchronize()
+    got = np.concatenate(outs)
+    assert got.shape == batch.shape
+    assert np.array_equal(got, batch)
+    assert st.position == (total, batch.shape[0])
+    st.close()
+
+
+def test_execute_host_equals_device(ppf):
+    import torch
+    N, T, S = 1024, 8, 40000
+    x, h = _rand(N, T, S, 55)
+    plan = ppf.Plan(N, T, h)
+    dev = plan(_dev(x)).cpu()
+    xh = torch.from_numpy(x).pin_memory()
+    host = plan.execute_host(xh)
+    assert torch.equal(dev, host)
+
+
+@pytest.mark.parametrize("N,T", [(1024, 8)])
+def test_full_size_realtime_second_sampled(ppf, N, T):
+    """One second of 6.5 GB/s complex64 at (N, T), as the benchmark launches it.
+
+    The whole stream runs in one ppf_execute; 1040 spectra (first 8, last 8,
+    1024 seeded) are checked against the oracle.
+    """
+    import torch
+    x, h, N, T, S = synth.realtime_second_config(N, T)
+    plan = ppf.Plan(N, T, h)
+    xd = _dev(x)
+    Y = plan(xd)
+    torch.cuda.synchronize()
+    rows = synth.sample_rows(S)
+    got = Y[torch.from_numpy(rows).to("cuda")].cpu().numpy()
+    ref = oracle.ppf_rows(x, h, N, T, rows)
+    assert synth.rel_l2(got, ref) <= TOL32
+    del xd, Y
+    torch.cuda.empty_cache()
