@@ -38,6 +38,7 @@ struct ppf_plan_s {
     int device = 0;
     void* d_h = nullptr;
     float2* d_tw = nullptr;
+    int* h_err = nullptr;    // mapped host word a kernel sets when a bounded wait gives up
     // staging for ppf_execute_host (allocated on first use)
     std::mutex host_mu;
     void* d_stage_in[2] = {nullptr, nullptr};
@@ -94,6 +95,7 @@ void free_plan_memory(ppf_plan_s* p)
 {
     if (p->d_h) cudaFree(p->d_h);
     if (p->d_tw) cudaFree(p->d_tw);
+    if (p->h_err) cudaFreeHost(p->h_err);
     for (int i = 0; i < 2; ++i) {
         if (p->d_stage_in[i]) cudaFree(p->d_stage_in[i]);
         if (p->d_stage_out[i]) cudaFree(p->d_stage_out[i]);
@@ -173,6 +175,12 @@ ppf_status_t ppf_plan_create(ppf_plan_t* out, int N, int T, const float* h_host,
         e = cudaMalloc(&p->d_tw, N * sizeof(float2));
         if (e == cudaSuccess) e = cudaMemcpy(p->d_tw, tw.data(), N * sizeof(float2), cudaMemcpyHostToDevice);
     }
+    int* d_err = nullptr;
+    if (e == cudaSuccess) e = cudaHostAlloc((void**)&p->h_err, sizeof(int), cudaHostAllocMapped);
+    if (e == cudaSuccess) {
+        *p->h_err = 0;
+        e = cudaHostGetDevicePointer((void**)&d_err, p->h_err, 0);
+    }
     if (e != cudaSuccess) {
         free_plan_memory(p);
         delete p;
@@ -186,6 +194,7 @@ ppf_status_t ppf_plan_create(ppf_plan_t* out, int N, int T, const float* h_host,
     v.h = p->d_h;
     v.tw = p->d_tw;
     v.sms = sms;
+    v.err = d_err;
     p->view = v;
     p->fir_view = v;
     p->fir_view.fir_only = 1;
@@ -229,6 +238,7 @@ ppf_status_t ppf_execute(ppf_plan_t plan, const void* d_in, void* d_out, int64_t
     const size_t out_bytes = (size_t)n_spectra * v.N * sizeof(float2);
     if (overlaps(d_in, in_bytes, d_out, out_bytes)) return PPF_ERR_MISALIGNED;
     if (pending_cuda_error()) return PPF_ERR_CUDA;
+    if (*(volatile int*)plan->h_err) return PPF_ERR_TIMEOUT;
     cudaError_t e;
     if (plan->flags & PPF_FLAG_FIR_ONLY)
         e = plan->fir_entry.launch(plan->fir_view, d_in, static_cast<float2*>(d_out), n_spectra,

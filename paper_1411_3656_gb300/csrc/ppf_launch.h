@@ -14,6 +14,7 @@ struct PlanView {
     int sms = 0;                  // multiprocessors of the plan's device
     int grid_cap = 0;             // resident CTAs for the chosen kernel (set by prepare)
     int fir_only = 0;             // test hook: store y instead of Y
+    int* err = nullptr;           // device-visible error word (mapped host memory)
 };
 
 using PrepareFn = cudaError_t (*)(PlanView&);

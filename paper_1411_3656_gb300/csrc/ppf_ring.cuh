@@ -1,0 +1,234 @@
+// Fused PPF kernel with a TMA-fed shared-memory ring (one CTA per SM).
+//
+// Each persistent CTA owns a contiguous band of output spectra and walks it in
+// blocks of RB spectra.  Input rows arrive through 1-D bulk copies
+// (cp.async.bulk, completion on an mbarrier per ring slot) into a ring of NCH
+// chunks of RB rows, so every input sample is read from HBM exactly once: the
+// T-1 rows a block shares with the next stay in the ring.  Per block:
+//
+//   1. wait for the chunk holding the block's newest rows (bounded wait);
+//   2. FIR (Section 2, Eq. 1): each thread owns channel pairs (2p, 2p+1), keeps
+//      their 2T coefficients in registers and produces RBT consecutive spectra
+//      from RBT+T-1 ring rows (register blocking: each shared-memory read feeds
+//      up to RBT multiply-adds per channel);
+//   3. refill the ring slot the block no longer needs;
+//   4. FFT of the RB filtered rows with Stockham radix-16 passes ping-ponging
+//      between two shared buffers; the last pass stores the spectra to global
+//      memory (coalesced, streaming).
+// Filtered data never leaves the chip.
+#pragma once
+
+#include "ppf_device.cuh"
+#include "ppf_ptx.cuh"
+
+namespace ppf {
+
+template <int N_, int T_, class In_, int NT_, int RB_, int NCH_>
+struct RingCfg {
+    static constexpr int N = N_, T = T_, NT = NT_, RB = RB_, NCH = NCH_;
+    using In = In_;
+    using raw = typename In::raw;
+    using coef_t = typename Coef<In>::type;
+    static constexpr int BPS = In::bytes;
+    static constexpr int RS = fft_row_stride(N);
+    static constexpr int PAIRS = N / 2;
+    static constexpr int G = PAIRS > NT ? PAIRS / NT : 1;     // channel pairs per thread
+    static constexpr int RG = PAIRS >= NT ? 1 : NT / PAIRS;   // row groups
+    static constexpr int RBT = RB / RG;                       // spectra per thread per block
+    static constexpr int KO = T >= 2 ? (T - 2) / RB + 1 : 0;  // chunks beyond the block's first
+    static constexpr int RING_ROWS = NCH * RB;
+    static constexpr int CHUNK_BYTES = RB * N * BPS;
+    static constexpr int RING_BYTES = NCH * CHUNK_BYTES;
+    static constexpr int BUF_SLOTS = RB * RS;
+    static constexpr int FFT_BYTES = 2 * BUF_SLOTS * 8;
+    static constexpr int SMEM = RING_BYTES + FFT_BYTES + NCH * 8;
+    static_assert(N >= 64, "ring kernel handles N >= 64");
+    static_assert(RB % RG == 0 && RBT >= 1, "rows per block must split over row groups");
+    static_assert(NCH >= KO + 2, "ring must hold a block's window plus one chunk in flight");
+    static_assert(CHUNK_BYTES % 16 == 0, "bulk copies move multiples of 16 bytes");
+};
+
+// One Stockham pass from `in` to `out` (or to global memory for the last pass).
+template <int N, int RB, int NT, int P>
+__device__ __forceinline__ void fft_pass_pp(const float2* in, float2* out, const float2* __restrict__ tw,
+                                            float2* __restrict__ Yb, int rows)
+{
+    constexpr int R = fft_radix(N, P);
+    constexpr int NS = fft_ns(N, P);
+    constexpr bool LAST = (P == fft_npass(N) - 1);
+    constexpr int IN_NS = P == 0 ? 0 : fft_ns(N, P - 1);
+    constexpr int IN_R = P == 0 ? 1 : fft_radix(N, P - 1);
+    constexpr int BPR = N / R;
+    constexpr int NB = RB * BPR;
+    constexpr int PER = (NB + NT - 1) / NT;
+#pragma unroll
+    for (int k = 0; k < PER; ++k) {
+        const int b = threadIdx.x + k * NT;
+        if (NB % NT == 0 || b < NB) {
+            const int row = b / BPR, j = b % BPR;
+            float2 v[R];
+            pass_load<N, R, IN_NS, IN_R>(in, row, j, v);
+            pass_twiddle<N, R, NS>(tw, j, v);
+            dft<R>(v);
+            if constexpr (LAST) {
+                if (row < rows) {
+                    float2* o = Yb + (int64_t)row * N + j;
+#pragma unroll
+                    for (int q = 0; q < R; ++q) __stcs(o + q * NS, v[q]);
+                }
+            } else {
+                pass_store<N, R, NS>(out, row, j, v);
+            }
+        }
+    }
+    if constexpr (!LAST) __syncthreads();
+}
+
+template <int N, int RB, int NT, int P = 0>
+__device__ __forceinline__ void fft_rows_pp(float2* a, float2* b, const float2* __restrict__ tw,
+                                            float2* __restrict__ Yb, int rows)
+{
+    if constexpr (P < fft_npass(N)) {
+        fft_pass_pp<N, RB, NT, P>(a, b, tw, Yb, rows);
+        fft_rows_pp<N, RB, NT, P + 1>(b, a, tw, Yb, rows);
+    }
+}
+
+template <class C>
+__global__ void __launch_bounds__(C::NT, 1)
+ppf_ring_kernel(const typename C::raw* __restrict__ x, const typename C::coef_t* __restrict__ h,
+                const float2* __restrict__ tw, float2* __restrict__ Y, int64_t S, int* __restrict__ err)
+{
+    constexpr int N = C::N, T = C::T, NT = C::NT, RB = C::RB, NCH = C::NCH, RS = C::RS;
+    constexpr int G = C::G, RBT = C::RBT, BPS = C::BPS, RING_ROWS = C::RING_ROWS;
+    using PV = typename Pair<typename C::In>::vec;
+
+    extern __shared__ __align__(128) unsigned char smem[];
+    unsigned char* ring = smem;
+    float2* bufA = reinterpret_cast<float2*>(smem + C::RING_BYTES);
+    float2* bufB = bufA + C::BUF_SLOTS;
+    uint64_t* bars = reinterpret_cast<uint64_t*>(smem + C::RING_BYTES + C::FFT_BYTES);
+
+    const int tid = threadIdx.x;
+    const int64_t nblk = (S + RB - 1) / RB;
+    const int64_t blo = nblk * blockIdx.x / gridDim.x;
+    const int64_t bhi = nblk * (blockIdx.x + 1) / gridDim.x;
+    if (blo >= bhi) return;
+    const int nb = (int)(bhi - blo);
+    const int64_t s_lo = blo * RB;
+    const int64_t s_hi = S < bhi * RB ? S : bhi * RB;
+    const int64_t in_end = s_hi + T - 1;  // input rows the band reads: [s_lo, in_end)
+    const int nchunks = (int)((in_end - s_lo + RB - 1) / RB);
+
+    uint64_t policy = 0;
+    if (tid == 0) {
+        for (int i = 0; i < NCH; ++i) mbar_init(&bars[i], 1);
+        fence_mbar_init();
+    }
+    __syncthreads();
+    int issued = 0;  // chunks issued so far (meaningful in thread 0)
+    auto issue = [&](int k) {
+        const int64_t r0 = s_lo + (int64_t)k * RB;
+        const int64_t rows = in_end - r0 < RB ? in_end - r0 : RB;
+        const uint32_t bytes = (uint32_t)(rows * N * BPS);
+        uint64_t* bar = &bars[k % NCH];
+        mbar_arrive_expect_tx(bar, bytes);
+        tma_load_1d(ring + (k % NCH) * C::CHUNK_BYTES, x + r0 * N, bytes, bar, policy);
+    };
+    if (tid == 0) {
+        policy = l2_evict_first_policy();
+        const int first = nchunks < NCH ? nchunks : NCH;
+        for (int k = 0; k < first; ++k) issue(k);
+        issued = first;
+    }
+
+    // Thread -> (row group, channel pairs); coefficients of its channels in registers.
+    const int rg = C::PAIRS >= NT ? 0 : tid / C::PAIRS;
+    const int pbase = C::PAIRS >= NT ? tid : tid % C::PAIRS;
+    const int i0 = rg * RBT;
+    float hr[G][T][2];
+#pragma unroll
+    for (int g = 0; g < G; ++g) {
+        const int c = 2 * (pbase + g * NT);
+#pragma unroll
+        for (int t = 0; t < T; ++t) {
+            hr[g][t][0] = coef_f(h[t * N + c]);
+            hr[g][t][1] = coef_f(h[t * N + c + 1]);
+        }
+    }
+
+    int waited = 0;  // chunks every thread has waited for
+    int rrb = 0;     // ring row of the block's first input row
+    bool failed = false;
+    for (int b = 0; b < nb; ++b) {
+        // 1. the block needs chunks b .. b+KO
+        bool ok = true;
+        const int need = (b + C::KO < nchunks ? b + C::KO : nchunks - 1) + 1;
+        for (; waited < need; ++waited) {
+            if (!mbar_wait_bounded(&bars[waited % NCH], (uint32_t)((waited / NCH) & 1))) {
+                ok = false;
+                break;
+            }
+        }
+        if (__syncthreads_or(!ok)) {
+            failed = true;
+            break;
+        }
+
+        // 2. FIR over the ring (Eq. 1), RBT spectra x 2 channels per pair
+#pragma unroll
+        for (int g = 0; g < G; ++g) {
+            const int c = 2 * (pbase + g * NT);
+            float2 a0[RBT], a1[RBT];
+#pragma unroll
+            for (int i = 0; i < RBT; ++i) {
+                a0[i] = make_float2(0.f, 0.f);
+                a1[i] = make_float2(0.f, 0.f);
+            }
+#pragma unroll
+            for (int u = 0; u < RBT + T - 1; ++u) {
+                int rr = rrb + i0 + u;
+                rr = rr >= RING_ROWS ? rr - RING_ROWS : rr;
+                const PV pv = *reinterpret_cast<const PV*>(ring + ((size_t)rr * N + c) * BPS);
+                float2 v0, v1;
+                Pair<typename C::In>::split(pv, v0, v1);
+#pragma unroll
+                for (int i = 0; i < RBT; ++i) {
+                    const int t = u - i;
+                    if (t >= 0 && t < T) {
+                        a0[i].x = fmaf(hr[g][t][0], v0.x, a0[i].x);
+                        a0[i].y = fmaf(hr[g][t][0], v0.y, a0[i].y);
+                        a1[i].x = fmaf(hr[g][t][1], v1.x, a1[i].x);
+                        a1[i].y = fmaf(hr[g][t][1], v1.y, a1[i].y);
+                    }
+                }
+            }
+#pragma unroll
+            for (int i = 0; i < RBT; ++i)
+                *reinterpret_cast<float4*>(bufA + (i0 + i) * RS + c) = make_float4(a0[i].x, a0[i].y, a1[i].x, a1[i].y);
+        }
+        __syncthreads();
+
+        // 3. chunk b is no longer needed: refill its slot
+        if (tid == 0 && issued < nchunks && issued == b + NCH) {
+            issue(issued);
+            ++issued;
+        }
+        rrb += RB;
+        rrb = rrb >= RING_ROWS ? rrb - RING_ROWS : rrb;
+
+        // 4. FFT of the RB rows; the last pass stores the spectra
+        const int64_t s0 = s_lo + (int64_t)b * RB;
+        const int rows = (int)(s_hi - s0 < RB ? s_hi - s0 : RB);
+        fft_rows_pp<N, RB, NT>(bufA, bufB, tw, Y + s0 * N, rows);
+    }
+    if (failed) {
+        if (tid == 0) {
+            // let the copies still in flight land before the CTA exits
+            for (int k = waited; k < issued; ++k) mbar_wait_bounded(&bars[k % NCH], (uint32_t)((k / NCH) & 1), kWaitLimitNs / 4);
+            atomicExch(err, 1);
+        }
+    }
+}
+
+}  // namespace ppf
