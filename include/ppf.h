@@ -69,6 +69,9 @@ typedef enum {
 #define PPF_FLAG_NONE 0u
 #define PPF_FLAG_FIR_ONLY 1u   /* test hook: write the FIR output y instead of Y */
 #define PPF_FLAG_GENERIC 2u    /* always use the general kernel (runtime T, any size) */
+/* Force specialised kernel variant i (0-based) of ppf_variant_count(N, T, dtype)
+ * instead of the tuned default; used by the autotuner. */
+#define PPF_FLAG_VARIANT(i) ((((unsigned)(i) + 1u) & 0xFFu) << 8)
 
 /*
  * ppf_plan_create -- build a plan for N channels and T taps (Section 2, Eq. 1).
@@ -159,6 +162,17 @@ const char* ppf_status_string(ppf_status_t status);
 /* Which kernel ppf_execute launches for this plan, as a static string (e.g.
  * "fused_ring" or "generic"); NULL for a NULL plan.  For tests and reports. */
 const char* ppf_plan_kernel_name(ppf_plan_t plan);
+
+/*
+ * ppf_variant_count -- number of compiled variants of the specialised kernels
+ * (thread count, spectra per block, ring depth, cluster size) for (N, T,
+ * dtype); 0 when only the general kernel covers the size.  Pure host query.
+ * ppf_variant_name -- static description of variant i, NULL if out of range.
+ * These are the tile shapes the autotuner times on the device; the fastest
+ * becomes the default the library picks.
+ */
+int ppf_variant_count(int N, int T, ppf_dtype_t dtype);
+const char* ppf_variant_name(int N, int T, ppf_dtype_t dtype, int i);
 
 /* Kernel launches this library has issued since load (for reports). */
 int64_t ppf_launch_count(void);

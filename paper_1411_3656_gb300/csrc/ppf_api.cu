@@ -21,7 +21,7 @@ namespace ppf {
 static std::atomic<int64_t> g_launches{0};
 void note_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
 
-KernelEntry select_fast_entry(int N, int T, int dtype);  // ppf_select.cu
+KernelEntry select_fast_entry(int N, int T, int dtype, int variant);  // ppf_select.cu
 
 }  // namespace ppf
 
@@ -139,7 +139,9 @@ ppf_status_t ppf_plan_create(ppf_plan_t* out, int N, int T, const float* h_host,
     if (bps == 0) return PPF_ERR_UNSUPPORTED;
     if (!is_pow2(N) || N < 4 || N > 4096 || T < 1 || T > 64) return PPF_ERR_UNSUPPORTED;
     if (in_dtype == PPF_IN_CI8 && N < 8) return PPF_ERR_UNSUPPORTED;
-    if (flags & ~(PPF_FLAG_FIR_ONLY | PPF_FLAG_GENERIC)) return PPF_ERR_INVALID_ARG;
+    if (flags & ~(PPF_FLAG_FIR_ONLY | PPF_FLAG_GENERIC | 0xFF00u)) return PPF_ERR_INVALID_ARG;
+    const int variant = (int)((flags >> 8) & 0xFFu) - 1;  // -1: tuned default
+    if (variant >= 0 && variant >= ppf_variant_count(N, T, in_dtype)) return PPF_ERR_UNSUPPORTED;
 
     ppf_plan_s* p = new (std::nothrow) ppf_plan_s();
     if (!p) return PPF_ERR_OUT_OF_MEMORY;
@@ -200,7 +202,7 @@ ppf_status_t ppf_plan_create(ppf_plan_t* out, int N, int T, const float* h_host,
     p->fir_view.fir_only = 1;
 
     p->fir_entry = ppf::generic_entry(N, (int)in_dtype);
-    p->entry = (flags & PPF_FLAG_GENERIC) ? p->fir_entry : ppf::select_fast_entry(N, T, (int)in_dtype);
+    p->entry = (flags & PPF_FLAG_GENERIC) ? p->fir_entry : ppf::select_fast_entry(N, T, (int)in_dtype, variant);
     if (!p->entry.launch) p->entry = p->fir_entry;
     if (!p->entry.launch || !p->fir_entry.launch) {
         free_plan_memory(p);

@@ -208,6 +208,45 @@ __device__ __forceinline__ void pass_twiddle(const float2* __restrict__ tw, int 
     }
 }
 
+// Twiddles of passes P.. of a length-N row for the butterfly index this thread
+// keeps in every block (j = threadIdx.x mod N/R; fixed because the block's
+// thread count is a multiple of N/R).  Loaded once per kernel into registers.
+template <int N, int NT, int P = 1, bool ANY = (P < fft_npass(N))>
+struct PassTwiddles {
+    static constexpr int R = fft_radix(N, P);
+    static constexpr int NS = fft_ns(N, P);
+    static_assert(NT % (N / R) == 0, "thread count must be a multiple of N/R");
+    float2 w[R - 1];
+    PassTwiddles<N, NT, P + 1> next;
+    __device__ __forceinline__ void load(const float2* __restrict__ tw)
+    {
+        const int k = (threadIdx.x % (N / R)) % NS;
+        constexpr int step = N / (NS * R);
+#pragma unroll
+        for (int r = 1; r < R; ++r) w[r - 1] = __ldg(tw + k * r * step);
+        next.load(tw);
+    }
+    template <int Q>
+    __device__ __forceinline__ const float2* get() const
+    {
+        if constexpr (Q == P) return w;
+        else return next.template get<Q>();
+    }
+};
+template <int N, int NT, int P>
+struct PassTwiddles<N, NT, P, false> {
+    __device__ __forceinline__ void load(const float2* __restrict__) {}
+    template <int Q>
+    __device__ __forceinline__ const float2* get() const { return nullptr; }
+};
+
+template <int R>
+__device__ __forceinline__ void apply_twiddles(const float2* w, float2 (&v)[R])
+{
+#pragma unroll
+    for (int r = 1; r < R; ++r) v[r] = cmul(v[r], w[r - 1]);
+}
+
 // Store the R outputs of butterfly j into row `row` of `buf` (padded for NS).
 template <int N, int R, int NS>
 __device__ __forceinline__ void pass_store(float2* buf, int row, int j, const float2 (&v)[R])

@@ -23,9 +23,9 @@
 
 namespace ppf {
 
-template <int N_, int T_, class In_, int NT_, int RB_, int NCH_>
+template <int N_, int T_, class In_, int NT_, int RB_, int NCH_, int MINB_ = 1>
 struct RingCfg {
-    static constexpr int N = N_, T = T_, NT = NT_, RB = RB_, NCH = NCH_;
+    static constexpr int N = N_, T = T_, NT = NT_, RB = RB_, NCH = NCH_, MINB = MINB_;
     using In = In_;
     using raw = typename In::raw;
     using coef_t = typename Coef<In>::type;
@@ -50,7 +50,7 @@ struct RingCfg {
 
 // One Stockham pass from `in` to `out` (or to global memory for the last pass).
 template <int N, int RB, int NT, int P>
-__device__ __forceinline__ void fft_pass_pp(const float2* in, float2* out, const float2* __restrict__ tw,
+__device__ __forceinline__ void fft_pass_pp(const float2* in, float2* out, const PassTwiddles<N, NT>& tw,
                                             float2* __restrict__ Yb, int rows)
 {
     constexpr int R = fft_radix(N, P);
@@ -68,7 +68,7 @@ __device__ __forceinline__ void fft_pass_pp(const float2* in, float2* out, const
             const int row = b / BPR, j = b % BPR;
             float2 v[R];
             pass_load<N, R, IN_NS, IN_R>(in, row, j, v);
-            pass_twiddle<N, R, NS>(tw, j, v);
+            if constexpr (P > 0) apply_twiddles<R>(tw.template get<P>(), v);
             dft<R>(v);
             if constexpr (LAST) {
                 if (row < rows) {
@@ -85,7 +85,7 @@ __device__ __forceinline__ void fft_pass_pp(const float2* in, float2* out, const
 }
 
 template <int N, int RB, int NT, int P = 0>
-__device__ __forceinline__ void fft_rows_pp(float2* a, float2* b, const float2* __restrict__ tw,
+__device__ __forceinline__ void fft_rows_pp(float2* a, float2* b, const PassTwiddles<N, NT>& tw,
                                             float2* __restrict__ Yb, int rows)
 {
     if constexpr (P < fft_npass(N)) {
@@ -95,7 +95,7 @@ __device__ __forceinline__ void fft_rows_pp(float2* a, float2* b, const float2* 
 }
 
 template <class C>
-__global__ void __launch_bounds__(C::NT, 1)
+__global__ void __launch_bounds__(C::NT, C::MINB)
 ppf_ring_kernel(const typename C::raw* __restrict__ x, const typename C::coef_t* __restrict__ h,
                 const float2* __restrict__ tw, float2* __restrict__ Y, int64_t S, int* __restrict__ err)
 {
@@ -156,6 +156,9 @@ ppf_ring_kernel(const typename C::raw* __restrict__ x, const typename C::coef_t*
             hr[g][t][1] = coef_f(h[t * N + c + 1]);
         }
     }
+
+    PassTwiddles<N, NT> twr;
+    twr.load(tw);
 
     int waited = 0;  // chunks every thread has waited for
     int rrb = 0;     // ring row of the block's first input row
@@ -220,7 +223,7 @@ ppf_ring_kernel(const typename C::raw* __restrict__ x, const typename C::coef_t*
         // 4. FFT of the RB rows; the last pass stores the spectra
         const int64_t s0 = s_lo + (int64_t)b * RB;
         const int rows = (int)(s_hi - s0 < RB ? s_hi - s0 : RB);
-        fft_rows_pp<N, RB, NT>(bufA, bufB, tw, Y + s0 * N, rows);
+        fft_rows_pp<N, RB, NT>(bufA, bufB, twr, Y + s0 * N, rows);
     }
     if (failed) {
         if (tid == 0) {

@@ -1,9 +1,14 @@
-// Instantiations and host launchers of the TMA-ring fused PPF kernel.
+// Host launchers of the TMA-ring kernel and the variant table shared by the
+// per-N translation units (each TU instantiates the variants of one N).
+#pragma once
+
+#include <cstdio>
+
 #include "ppf_launch.h"
 #include "ppf_ring.cuh"
 
 namespace ppf {
-namespace {
+namespace ring_detail {
 
 template <class C>
 cudaError_t prepare_ring(PlanView& p)
@@ -34,42 +39,21 @@ cudaError_t launch_ring(const PlanView& p, const void* in, float2* out, int64_t 
 template <class C>
 KernelEntry entry()
 {
+    static char name[64];
+    std::snprintf(name, sizeof(name), "ring:nt%d:rb%d:nch%d:b%d", C::NT, C::RB, C::NCH, C::MINB);
     KernelEntry e;
-    e.name = "ring";
+    e.name = name;
     e.prepare = prepare_ring<C>;
     e.launch = launch_ring<C>;
     return e;
 }
 
-// (N, T) -> ring configuration <threads, rows per block, ring chunks>; shared
-// memory stays under the 227 KB a CTA may use.
-template <class In>
-KernelEntry ring_for(int N, int T)
-{
-#define PPF_RING(NN, TT, NT, RB, NCH) \
-    if (N == NN && T == TT) return entry<RingCfg<NN, TT, In, NT, RB, NCH>>();
-    PPF_RING(256, 4, 256, 16, 4)
-    PPF_RING(256, 8, 256, 16, 4)
-    PPF_RING(256, 16, 256, 16, 4)
-    PPF_RING(256, 32, 256, 16, 4)
-    PPF_RING(512, 4, 256, 8, 4)
-    PPF_RING(512, 8, 256, 8, 4)
-    PPF_RING(512, 16, 256, 8, 4)
-    PPF_RING(1024, 4, 256, 4, 4)
-    PPF_RING(1024, 8, 256, 4, 4)
-    PPF_RING(2048, 4, 256, 2, 4)
-#undef PPF_RING
-    return KernelEntry{};
-}
-
-}  // namespace
-
-KernelEntry ring_entry(int N, int T, int dtype)
-{
-    switch (dtype) {
-    case 0: return ring_for<InC32>(N, T);
-    default: return KernelEntry{};
-    }
-}
-
+}  // namespace ring_detail
 }  // namespace ppf
+
+// Walk a variant list: PPF_RV(NN, TT, NT, RB, NCH, MINB) entries for one input type.
+#define PPF_RV(NN, TT, NT, RB, NCH, MINB)                                                      \
+    if (N == NN && T == TT) {                                                                  \
+        if (idx == want && out) *out = ring_detail::entry<RingCfg<NN, TT, In, NT, RB, NCH, MINB>>(); \
+        ++idx;                                                                                 \
+    }

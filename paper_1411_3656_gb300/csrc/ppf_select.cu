@@ -1,17 +1,74 @@
-// Kernel selection for a plan: the specialised kernel for (N, T, dtype) when
-// one is compiled in, otherwise an empty entry (the plan then uses the general
-// kernel, which handles every supported size).
+// Kernel selection for a plan.  Every (N, T, dtype) has an ordered list of
+// compiled variants of the specialised kernels; the default is the variant the
+// autotuner measured fastest on GB300 (ppf_tuned.inc), else the first.  When no
+// specialised variant exists the plan uses the general kernel, which handles
+// every supported size.
+#include "ppf.h"
 #include "ppf_launch.h"
+
+#include <cstring>
 
 namespace ppf {
 
-KernelEntry ring_entry(int N, int T, int dtype);  // ppf_ring.cu
+int ring_variants_c32_small(int N, int T, int want, KernelEntry* out);
+int ring_variants_c32_large(int N, int T, int want, KernelEntry* out);
 
-KernelEntry select_fast_entry(int N, int T, int dtype)
+// Number of variants for (N, T, dtype); fills *out with variant `want` if it exists.
+int variants(int N, int T, int dtype, int want, KernelEntry* out)
 {
-    KernelEntry e = ring_entry(N, T, dtype);
-    if (e.launch) return e;
-    return KernelEntry{};
+    int n = 0;
+    if (dtype == 0) {
+        KernelEntry e;
+        int c = ring_variants_c32_small(N, T, want - n, &e);
+        if (want - n >= 0 && want - n < c && out) *out = e;
+        n += c;
+        c = ring_variants_c32_large(N, T, want - n, &e);
+        if (want - n >= 0 && want - n < c && out) *out = e;
+        n += c;
+    }
+    return n;
+}
+
+static int tuned_variant(int N, int T, int dtype)
+{
+    // An entry applies only while its variant still has the recorded name.
+#define PPF_TUNED(NN, TT, DT, V, NAME)                                                      \
+    if (N == NN && T == TT && dtype == DT) {                                                \
+        KernelEntry e;                                                                      \
+        if (V < variants(N, T, dtype, -1, nullptr) && (variants(N, T, dtype, V, &e), true) && \
+            e.name && std::strcmp(e.name, NAME) == 0)                                      \
+            return V;                                                                       \
+        return 0;                                                                           \
+    }
+#if __has_include("ppf_tuned.inc")
+#include "ppf_tuned.inc"
+#endif
+#undef PPF_TUNED
+    return 0;
+}
+
+KernelEntry select_fast_entry(int N, int T, int dtype, int variant)
+{
+    KernelEntry e;
+    const int n = variants(N, T, dtype, -1, nullptr);
+    if (n == 0) return KernelEntry{};
+    int v = variant >= 0 ? variant : tuned_variant(N, T, dtype);
+    if (v >= n) v = 0;
+    variants(N, T, dtype, v, &e);
+    return e;
 }
 
 }  // namespace ppf
+
+extern "C" int ppf_variant_count(int N, int T, ppf_dtype_t dtype)
+{
+    return ppf::variants(N, T, (int)dtype, -1, nullptr);
+}
+
+extern "C" const char* ppf_variant_name(int N, int T, ppf_dtype_t dtype, int i)
+{
+    ppf::KernelEntry e;
+    if (i < 0 || i >= ppf::variants(N, T, (int)dtype, -1, nullptr)) return nullptr;
+    ppf::variants(N, T, (int)dtype, i, &e);
+    return e.name;
+}

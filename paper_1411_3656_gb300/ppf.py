@@ -29,7 +29,8 @@ FLAG_GENERIC = 2
 #: every entry point declared in include/ppf.h
 EXPORTS = ("ppf_plan_create", "ppf_plan_destroy", "ppf_execute", "ppf_execute_host",
            "ppf_stream_open", "ppf_stream_push", "ppf_stream_position", "ppf_stream_close",
-           "ppf_status_string", "ppf_plan_kernel_name", "ppf_launch_count")
+           "ppf_status_string", "ppf_plan_kernel_name", "ppf_launch_count", "ppf_variant_count",
+           "ppf_variant_name")
 
 
 class PPFError(RuntimeError):
@@ -66,6 +67,8 @@ def load(path: str | None = None):
             "ppf_status_string": ([i32], ctypes.c_char_p),
             "ppf_plan_kernel_name": ([vp], ctypes.c_char_p),
             "ppf_launch_count": ([], i64),
+            "ppf_variant_count": ([i32, i32, i32], i32),
+            "ppf_variant_name": ([i32, i32, i32, i32], ctypes.c_char_p),
         }
         for name, (args, res) in sig.items():
             fn = getattr(lib, name)
@@ -151,6 +154,20 @@ def ppf_plan_kernel_name(plan: int) -> str:
 
 def ppf_launch_count() -> int:
     return int(load().ppf_launch_count())
+
+
+def ppf_variant_count(N: int, T: int, dtype: str = "c32") -> int:
+    return int(load().ppf_variant_count(int(N), int(T), DTYPES[dtype]))
+
+
+def ppf_variant_name(N: int, T: int, dtype: str, i: int) -> str | None:
+    r = load().ppf_variant_name(int(N), int(T), DTYPES[dtype], int(i))
+    return r.decode() if r else None
+
+
+def flag_variant(i: int) -> int:
+    """PPF_FLAG_VARIANT(i): force specialised kernel variant i."""
+    return ((int(i) + 1) & 0xFF) << 8
 
 
 # -- torch-facing wrappers -----------------------------------------------------

@@ -203,3 +203,21 @@ def test_full_size_realtime_second_sampled(ppf, N, T):
     assert synth.rel_l2(got, ref) <= TOL32
     del xd, Y
     torch.cuda.empty_cache()
+
+
+VARIANT_CELLS = [(N, T) for N in (128, 256, 512, 1024, 2048, 4096) for T in (4, 8, 16, 32)]
+
+
+@pytest.mark.parametrize("N,T", VARIANT_CELLS)
+def test_every_variant(ppf, N, T):
+    """Every compiled tile-shape variant of the specialised kernels matches the oracle."""
+    n = ppf.ppf_variant_count(N, T, "c32")
+    if n == 0:
+        pytest.skip("no specialised variant for this size")
+    S = max(3, 40960 // N) + 3
+    x, h = _rand(N, T, S, 2000 + N + T)
+    ref = oracle.ppf(x, h, N, T, S)
+    for i in range(n):
+        Y, kern = _run(ppf, x, h, N, T, S, flags=ppf.flag_variant(i))
+        assert kern == ppf.ppf_variant_name(N, T, "c32", i)
+        assert synth.rel_l2(Y, ref) <= TOL32, kern
