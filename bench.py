@@ -52,6 +52,7 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=15.0, help="CPU budget of the oracle baseline")
     ap.add_argument("--cells-out", default="", help="also write the per-cell table as JSON here")
+    ap.add_argument("--variant", type=int, default=-1, help="force kernel variant i (profiling one cell)")
     return ap.parse_args()
 
 
@@ -254,7 +255,8 @@ def run_ours(args):
     plans = []
     for N, T in cells:
         S = spectra_of(args, N, T)
-        plans.append((N, T, S, ppf.Plan(N, T, synth.hamming_sinc(N, T), dtype)))
+        flags = ppf.flag_variant(args.variant) if args.variant >= 0 else 0
+        plans.append((N, T, S, ppf.Plan(N, T, synth.hamming_sinc(N, T), dtype, flags)))
     stream = torch.cuda.current_stream(dev)
     sp = stream.cuda_stream
     xin, yout = x_dev.data_ptr(), y_dev.data_ptr()

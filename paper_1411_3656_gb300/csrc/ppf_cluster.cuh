@@ -15,10 +15,14 @@
 //   2. takes the N2-point DFTs over c2 for each of its c1 (Stockham passes in
 //      shared memory, element stride C1);
 //   3. multiplies by W_N^{c1*k2} and stores each result into the shared
-//      memory of the CTA that owns bin group k2 (distributed shared memory,
-//      K2 = N2/P bins per CTA);
-//   4. after one cluster barrier, takes the N1-point DFTs over c1 of its K2
-//      bin groups and stores the spectra (runs of K2 consecutive bins).
+//      memory of the CTA that owns bin group k2 (st.async into distributed
+//      shared memory, K2 = N2/P bins per CTA, completion counted in bytes on
+//      the owner's mbarrier, so no cluster-wide fence is needed);
+//   4. once its mbarrier has seen every byte, takes the N1-point DFTs over
+//      c1 of its K2 bin groups and stores the spectra (runs of K2
+//      consecutive bins); after its last read of the exchange buffer it
+//      arrives on each peer's "buffer free" mbarrier.
+// The exchange buffer is double-buffered per block parity.
 // Input is read from HBM once, filtered data never leaves the cluster.
 #pragma once
 
@@ -66,7 +70,8 @@ struct ClusterCfg {
     static constexpr int A_SLOTS = RB * RSB;
     static constexpr int RS1 = stage2_stride(N1, K2);
     static constexpr int X_SLOTS = RB * K2 * RS1;
-    static constexpr int SMEM = RING_BYTES + (A_SLOTS + 2 * X_SLOTS) * 8 + NCH * 8;
+    static constexpr int XBYTES = RB * K2 * N1 * 8;  // bytes each CTA receives per block
+    static constexpr int SMEM = RING_BYTES + (A_SLOTS + 2 * X_SLOTS) * 8 + (NCH + 4) * 8;
     static_assert(P >= 2 && P <= 8, "portable cluster sizes");
     static_assert(C1 >= 2 && C1 % 2 == 0 && (C1 * BPS) % 16 == 0, "TMA box rows must be 16-byte multiples");
     static_assert(K2 >= 1 && N2 <= 256 && C1 <= 256 && RB <= 256, "TMA box limits");
@@ -119,7 +124,8 @@ struct Stage1Out {
     static_assert(C::NT % (C::C1 * (L / R)) == 0, "thread count must be a multiple of the butterflies per row");
     float2 w[R];
     uint32_t addr[R];
-    __device__ __forceinline__ void load(const float2* __restrict__ tw, float2* X, int rank)
+    uint32_t rbar[R];  // the owner's "exchange full" mbarrier for block parity 0 (+8 for parity 1)
+    __device__ __forceinline__ void load(const float2* __restrict__ tw, float2* X, uint64_t* xfull, int rank)
     {
         constexpr int BPR = C::C1 * (L / R);
         const int rem = threadIdx.x % BPR;
@@ -132,6 +138,7 @@ struct Stage1Out {
             w[q] = __ldg(tw + (int)(((int64_t)c1 * k2) % C::N));
             const int dst = k2 / C::K2, k2l = k2 % C::K2;
             addr[q] = map_shared_rank(xbase + (uint32_t)((k2l * C::RS1 + c1) * 8), (uint32_t)dst);
+            rbar[q] = map_shared_rank(smem_u32(xfull), (uint32_t)dst);
         }
     }
 };
@@ -140,7 +147,7 @@ struct Stage1Out {
 // place).  The last pass sends its outputs to the owning CTAs' X buffers.
 template <class C, int PP>
 __device__ __forceinline__ void stage1_pass(float2* A, const StageTwiddles<C::N2, C::C1, C::NT>& tw,
-                                            const Stage1Out<C>& so, uint32_t xoff)
+                                            const Stage1Out<C>& so, uint32_t xoff, uint32_t boff)
 {
     constexpr int L = C::N2, NT = C::NT, C1 = C::C1, RB = C::RB, RSB = C::RSB;
     constexpr int R = fft_radix(L, PP), NS = fft_ns(L, PP);
@@ -180,28 +187,28 @@ __device__ __forceinline__ void stage1_pass(float2* A, const StageTwiddles<C::N2
         } else {
             const uint32_t roff = xoff + (uint32_t)(row * C::K2 * C::RS1 * 8);
 #pragma unroll
-            for (int q = 0; q < R; ++q) st_cluster_f2(so.addr[q] + roff, cmul(v[k][q], so.w[q]));
+            for (int q = 0; q < R; ++q) st_async_f2(so.addr[q] + roff, cmul(v[k][q], so.w[q]), so.rbar[q] + boff);
         }
     }
     if constexpr (!LAST) __syncthreads();
 }
 
 template <class C, int PP = 0>
-__device__ __forceinline__ void stage1(float2* A, const StageTwiddles<C::N2, C::C1, C::NT>& tw,
-                                       const Stage1Out<C>& so, uint32_t xoff)
+__device__ __forceinline__ void stage1_upto_last(float2* A, const StageTwiddles<C::N2, C::C1, C::NT>& tw,
+                                                 const Stage1Out<C>& so)
 {
-    if constexpr (PP < fft_npass(C::N2)) {
-        stage1_pass<C, PP>(A, tw, so, xoff);
-        stage1<C, PP + 1>(A, tw, so, xoff);
+    if constexpr (PP < fft_npass(C::N2) - 1) {
+        stage1_pass<C, PP>(A, tw, so, 0, 0);
+        stage1_upto_last<C, PP + 1>(A, tw, so);
     }
 }
 
 // Stage 2, pass PP: N1-point transforms over c1 of rows (row, k2l) in X (in
 // place); bin group k2l varies fastest across threads so the last pass stores
 // runs of K2 consecutive bins.
-template <class C, int PP>
+template <class C, int PP, class F>
 __device__ __forceinline__ void stage2_pass(float2* X, const StageTwiddles<C::N1, C::K2, C::NT>& tw,
-                                            float2* __restrict__ Yb, int rows, int rank)
+                                            float2* __restrict__ Yb, int rows, int rank, F&& after_last_read)
 {
     constexpr int L = C::N1, NT = C::NT, K2 = C::K2, RB = C::RB, RS1 = C::RS1;
     constexpr int R = fft_radix(L, PP), NS = fft_ns(L, PP);
@@ -230,9 +237,15 @@ __device__ __forceinline__ void stage2_pass(float2* X, const StageTwiddles<C::N1
     for (int k = 0; k < PER; ++k) {
         const int b = threadIdx.x + k * NT;
         if (NB % NT != 0 && b >= NB) continue;
-        const int row = b / BPR, rem = b % BPR, k2l = rem % K2, j = rem / K2;
         if constexpr (PP > 0) apply_twiddles<R>(tw.template get<PP>(), v[k]);
         dft<R>(v[k]);
+    }
+    if constexpr (LAST) after_last_read();
+#pragma unroll
+    for (int k = 0; k < PER; ++k) {
+        const int b = threadIdx.x + k * NT;
+        if (NB % NT != 0 && b >= NB) continue;
+        const int row = b / BPR, rem = b % BPR, k2l = rem % K2, j = rem / K2;
         if constexpr (!LAST) {
             float2* x = X + (row * K2 + k2l) * RS1;
             const int base = (j / NS) * NS * R + (j % NS);
@@ -247,13 +260,13 @@ __device__ __forceinline__ void stage2_pass(float2* X, const StageTwiddles<C::N1
     if constexpr (!LAST) __syncthreads();
 }
 
-template <class C, int PP = 0>
+template <class C, int PP = 0, class F>
 __device__ __forceinline__ void stage2(float2* X, const StageTwiddles<C::N1, C::K2, C::NT>& tw,
-                                       float2* __restrict__ Yb, int rows, int rank)
+                                       float2* __restrict__ Yb, int rows, int rank, F&& after_last_read)
 {
     if constexpr (PP < fft_npass(C::N1)) {
-        stage2_pass<C, PP>(X, tw, Yb, rows, rank);
-        stage2<C, PP + 1>(X, tw, Yb, rows, rank);
+        stage2_pass<C, PP>(X, tw, Yb, rows, rank, after_last_read);
+        stage2<C, PP + 1>(X, tw, Yb, rows, rank, after_last_read);
     }
 }
 
@@ -271,6 +284,8 @@ ppf_cluster_kernel(const __grid_constant__ CUtensorMap xmap, const typename C::c
     float2* A = reinterpret_cast<float2*>(smem + C::RING_BYTES);
     float2* X = A + C::A_SLOTS;  // two buffers of X_SLOTS
     uint64_t* bars = reinterpret_cast<uint64_t*>(smem + C::RING_BYTES + (C::A_SLOTS + 2 * C::X_SLOTS) * 8);
+    uint64_t* xfull = bars + NCH;      // [2]: every byte of X[parity] has arrived
+    uint64_t* xfree = bars + NCH + 2;  // [2]: every owner has finished reading its X[parity]
 
     const int tid = threadIdx.x;
     const int rank = (int)cluster_ctarank();
@@ -286,9 +301,14 @@ ppf_cluster_kernel(const __grid_constant__ CUtensorMap xmap, const typename C::c
 
     if (tid == 0) {
         for (int i = 0; i < NCH; ++i) mbar_init(&bars[i], 1);
+        for (int i = 0; i < 2; ++i) {
+            mbar_init(&xfull[i], 1);
+            mbar_init(&xfree[i], P);
+        }
         fence_mbar_init();
     }
-    // every CTA of the cluster is running before any distributed-memory store
+    // every CTA of the cluster is running, with its mbarriers initialised,
+    // before any distributed-memory store or remote arrive
     cluster_arrive_release();
     cluster_wait_acquire();
 
@@ -328,76 +348,95 @@ ppf_cluster_kernel(const __grid_constant__ CUtensorMap xmap, const typename C::c
     StageTwiddles<C::N1, C::K2, NT> tw2;
     tw2.load(tw, N);
     Stage1Out<C> so;
-    so.load(tw, X, rank);
+    so.load(tw, X, xfull, rank);
 
     int waited = 0, rrb = 0;
     bool failed = false;
-    for (int b = 0; b < nb; ++b) {
-        bool ok = true;
-        if (!failed) {
-            const int need = (b + C::KO < nchunks ? b + C::KO : nchunks - 1) + 1;
-            for (; waited < need; ++waited) {
-                if (!mbar_wait_bounded(&bars[waited % NCH], (uint32_t)((waited / NCH) & 1))) {
-                    ok = false;
-                    break;
-                }
-            }
-        }
-        // A failed wait is recorded and the cluster keeps its barrier schedule
-        // (no early exit, so no CTA waits on one that has left).
-        if (__syncthreads_or(!ok)) failed = true;
-
-        // 1. FIR over the ring
-#pragma unroll
-        for (int g = 0; g < G; ++g) {
-            const int pp = pbase + g * NT;
-            const int l = (pp / (C1 / 2)) * C1 + 2 * (pp % (C1 / 2));
-            float2 a0[RBT], a1[RBT];
-#pragma unroll
-            for (int i = 0; i < RBT; ++i) {
-                a0[i] = make_float2(0.f, 0.f);
-                a1[i] = make_float2(0.f, 0.f);
-            }
-#pragma unroll
-            for (int u = 0; u < RBT + T - 1; ++u) {
-                int rr = rrb + i0 + u;
-                rr = rr >= RING_ROWS ? rr - RING_ROWS : rr;
-                const PV pv = *reinterpret_cast<const PV*>(ring + ((size_t)rr * NC + l) * BPS);
-                float2 v0, v1;
-                Pair<typename C::In>::split(pv, v0, v1);
-#pragma unroll
-                for (int i = 0; i < RBT; ++i) {
-                    const int t = u - i;
-                    if (t >= 0 && t < T) {
-                        a0[i].x = fmaf(hr[g][t][0], v0.x, a0[i].x);
-                        a0[i].y = fmaf(hr[g][t][0], v0.y, a0[i].y);
-                        a1[i].x = fmaf(hr[g][t][1], v1.x, a1[i].x);
-                        a1[i].y = fmaf(hr[g][t][1], v1.y, a1[i].y);
+    // Software pipeline: iteration b filters and sends block b, then finishes
+    // block b-1, whose exchange data arrived while block b was being filtered.
+    for (int b = 0; b <= nb; ++b) {
+        if (b < nb) {
+            bool ok = true;
+            if (!failed) {
+                const int need = (b + C::KO < nchunks ? b + C::KO : nchunks - 1) + 1;
+                for (; waited < need; ++waited) {
+                    if (!mbar_wait_bounded(&bars[waited % NCH], (uint32_t)((waited / NCH) & 1))) {
+                        ok = false;
+                        break;
                     }
                 }
             }
+            // A failed wait is recorded and the cluster keeps its schedule (no
+            // early exit, so no CTA waits on one that has left).
+            if (__syncthreads_or(!ok)) failed = true;
+
+            // 1. FIR over the ring
 #pragma unroll
-            for (int i = 0; i < RBT; ++i)
-                *reinterpret_cast<float4*>(A + (i0 + i) * C::RSB + l) = make_float4(a0[i].x, a0[i].y, a1[i].x, a1[i].y);
-        }
-        __syncthreads();
-        if (tid == 0 && !failed && issued < nchunks && issued == b + NCH) {
-            issue(issued);
-            ++issued;
-        }
-        rrb += RB;
-        rrb = rrb >= RING_ROWS ? rrb - RING_ROWS : rrb;
+            for (int g = 0; g < G; ++g) {
+                const int pp = pbase + g * NT;
+                const int l = (pp / (C1 / 2)) * C1 + 2 * (pp % (C1 / 2));
+                float2 a0[RBT], a1[RBT];
+#pragma unroll
+                for (int i = 0; i < RBT; ++i) {
+                    a0[i] = make_float2(0.f, 0.f);
+                    a1[i] = make_float2(0.f, 0.f);
+                }
+#pragma unroll
+                for (int u = 0; u < RBT + T - 1; ++u) {
+                    int rr = rrb + i0 + u;
+                    rr = rr >= RING_ROWS ? rr - RING_ROWS : rr;
+                    const PV pv = *reinterpret_cast<const PV*>(ring + ((size_t)rr * NC + l) * BPS);
+                    float2 v0, v1;
+                    Pair<typename C::In>::split(pv, v0, v1);
+#pragma unroll
+                    for (int i = 0; i < RBT; ++i) {
+                        const int t = u - i;
+                        if (t >= 0 && t < T) {
+                            a0[i].x = fmaf(hr[g][t][0], v0.x, a0[i].x);
+                            a0[i].y = fmaf(hr[g][t][0], v0.y, a0[i].y);
+                            a1[i].x = fmaf(hr[g][t][1], v1.x, a1[i].x);
+                            a1[i].y = fmaf(hr[g][t][1], v1.y, a1[i].y);
+                        }
+                    }
+                }
+#pragma unroll
+                for (int i = 0; i < RBT; ++i)
+                    *reinterpret_cast<float4*>(A + (i0 + i) * C::RSB + l) =
+                        make_float4(a0[i].x, a0[i].y, a1[i].x, a1[i].y);
+            }
+            __syncthreads();
+            if (tid == 0 && !failed && issued < nchunks && issued == b + NCH) {
+                issue(issued);
+                ++issued;
+            }
+            rrb += RB;
+            rrb = rrb >= RING_ROWS ? rrb - RING_ROWS : rrb;
 
-        // 2-3. N2-point DFTs, four-step twiddle, scatter to the owning CTAs
-        const uint32_t xoff = (uint32_t)((b & 1) * C::X_SLOTS * 8);
-        stage1<C>(A, tw1, so, xoff);
-        cluster_arrive_release();
-        cluster_wait_acquire();
-
-        // 4. N1-point DFTs of this CTA's bin groups, store the spectra
-        const int64_t s0 = s_lo + (int64_t)b * RB;
-        const int rows = (int)(s_hi - s0 < RB ? s_hi - s0 : RB);
-        stage2<C>(X + (b & 1) * C::X_SLOTS, tw2, Y + s0 * N, rows, rank);
+            // 2-3. N2-point DFTs, four-step twiddle, send to the owning CTAs
+            const int par = b & 1;
+            if (tid == 0) mbar_arrive_expect_tx(&xfull[par], (uint32_t)C::XBYTES);
+            stage1_upto_last<C>(A, tw1, so);
+            // the owners have finished reading X[par] of block b-2
+            bool okf = true;
+            if (b >= 2 && !failed) okf = mbar_wait_bounded(&xfree[par], (uint32_t)(((b >> 1) - 1) & 1));
+            if (__syncthreads_or(!okf)) failed = true;
+            stage1_pass<C, fft_npass(C::N2) - 1>(A, tw1, so, (uint32_t)(par * C::X_SLOTS * 8),
+                                                 (uint32_t)(par * 8));
+        }
+        if (b >= 1) {
+            // 4. block b-1: once every byte of X[par] is here, N1-point DFTs and store
+            const int bp = b - 1, par = bp & 1;
+            bool okf = true;
+            if (!failed) okf = mbar_wait_bounded(&xfull[par], (uint32_t)((bp >> 1) & 1));
+            if (__syncthreads_or(!okf)) failed = true;
+            const int64_t s0 = s_lo + (int64_t)bp * RB;
+            const int rows = (int)(s_hi - s0 < RB ? s_hi - s0 : RB);
+            stage2<C>(X + par * C::X_SLOTS, tw2, Y + s0 * N, rows, rank, [&] {
+                // every thread's last reads of X[par] have returned; free it for the senders
+                __syncthreads();
+                if (tid < P) mbar_arrive_remote(map_shared_rank(smem_u32(&xfree[par]), (uint32_t)tid));
+            });
+        }
     }
     // no CTA leaves while a peer may still store into its shared memory
     cluster_arrive_release();

@@ -8,12 +8,12 @@ static int cluster_variants_a(int N, int T, int want, KernelEntry* out)
 {
     int idx = 0;
     PPF_CV(512, 32, 2, 32, 128, 8, 6, 1)
-    PPF_CV(1024, 8, 2, 32, 256, 4, 4, 1)
-    PPF_CV(1024, 16, 2, 32, 256, 4, 6, 1)
+    PPF_CV(1024, 8, 2, 32, 256, 4, 4, 1) PPF_CV(1024, 8, 2, 32, 256, 4, 5, 1) PPF_CV(1024, 8, 4, 32, 256, 8, 3, 1)
+    PPF_CV(1024, 16, 2, 32, 256, 4, 6, 1) PPF_CV(1024, 16, 4, 64, 256, 8, 4, 1) PPF_CV(1024, 16, 4, 32, 256, 8, 4, 1)
     PPF_CV(1024, 32, 4, 64, 256, 8, 6, 1)
-    PPF_CV(2048, 8, 4, 64, 256, 4, 4, 1) PPF_CV(2048, 8, 4, 64, 256, 8, 3, 1)
-    PPF_CV(2048, 16, 4, 64, 256, 4, 6, 1)
-    PPF_CV(2048, 32, 8, 64, 256, 8, 6, 1)
+    PPF_CV(2048, 8, 4, 64, 256, 4, 4, 1) PPF_CV(2048, 8, 4, 64, 256, 8, 3, 1) PPF_CV(2048, 8, 4, 64, 256, 4, 5, 1)
+    PPF_CV(2048, 16, 4, 64, 256, 4, 6, 1) PPF_CV(2048, 16, 8, 64, 256, 8, 5, 1)
+    PPF_CV(2048, 32, 8, 64, 256, 8, 6, 1) PPF_CV(2048, 32, 8, 64, 128, 4, 10, 2)
     return idx;
 }
 

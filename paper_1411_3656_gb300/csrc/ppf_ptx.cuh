@@ -161,4 +161,20 @@ __device__ __forceinline__ void st_cluster_f4(uint32_t addr, float4 v)
                  : "memory");
 }
 
+// Asynchronous store of 8 bytes into a peer CTA's shared memory; completion is
+// counted (8 bytes of complete_tx) on the peer's mbarrier `rbar`.  No fence is
+// needed: the receiver observes the data through that mbarrier.
+__device__ __forceinline__ void st_async_f2(uint32_t addr, float2 v, uint32_t rbar)
+{
+    asm volatile("st.async.shared::cluster.mbarrier::complete_tx::bytes.v2.f32 [%0], {%1, %2}, [%3];" ::"r"(addr),
+                 "f"(v.x), "f"(v.y), "r"(rbar)
+                 : "memory");
+}
+
+// Arrive once on an mbarrier of a peer CTA (cluster shared-memory address).
+__device__ __forceinline__ void mbar_arrive_remote(uint32_t rbar)
+{
+    asm volatile("mbarrier.arrive.shared::cluster.b64 _, [%0];" ::"r"(rbar) : "memory");
+}
+
 }  // namespace ppf
