@@ -149,6 +149,31 @@ ppf_status_t ppf_stream_push(ppf_stream_t s, const void* d_chunk, int64_t n_samp
                              void* d_out, int64_t out_capacity_spectra,
                              int64_t* n_spectra_out, void* stream);
 
+/*
+ * ppf_execute_noalloc -- the whole PPF with no plan and no device allocation.
+ * The paper has no counterpart; this is for callers that cannot allocate
+ * device memory when they need a filter bank: code running while a stream is
+ * captured into a CUDA graph (cudaMalloc is not allowed there), plug-ins whose
+ * host framework owns all device memory and forbids cudaMalloc/cudaFree, and
+ * real-time threads that must not block on the allocator's device-wide
+ * synchronisation.
+ *   N, T, dtype  as for ppf_plan_create; N at most 4096 (the scratch limit:
+ *                larger N returns PPF_ERR_UNSUPPORTED).
+ *   d_h          device array of N*T float coefficients, h[t*N + c] (FP32 for
+ *                every input type).  Read only.
+ *   d_in, d_out, n_spectra, stream  as for ppf_execute.
+ * Runs the general fused kernel.  Its FFT twiddle table is scratch kept in one
+ * library-wide static device array of 4096 complex values (32 KiB per GPU
+ * that loads the library, held until exit), rewritten by every call on the
+ * call's stream.  Calls that overlap on the GPU (different streams, or the
+ * same stream from several threads without ordering) share that array and
+ * race.  The first call on each device runs a one-time set-up (symbol
+ * address, kernel attributes); make that first call before any stream capture
+ * begins.  Allocates nothing, frees nothing, calls no allocating library.
+ */
+ppf_status_t ppf_execute_noalloc(int N, int T, ppf_dtype_t dtype, const float* d_h, const void* d_in,
+                                 void* d_out, int64_t n_spectra, void* stream);
+
 /* Total samples pushed and spectra emitted so far (either pointer may be NULL). */
 ppf_status_t ppf_stream_position(ppf_stream_t s, int64_t* samples_in, int64_t* spectra_out);
 

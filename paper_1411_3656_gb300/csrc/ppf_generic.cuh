@@ -76,10 +76,10 @@ __device__ __forceinline__ void fft_block(float2* buf, const float2* __restrict_
     }
 }
 
-template <int N, class In>
+template <int N, class In, class Cf = typename Coef<In>::type>
 __global__ void __launch_bounds__(kGenericThreads)
 ppf_generic_kernel(const typename In::raw* __restrict__ x,
-                   const typename Coef<In>::type* __restrict__ h,
+                   const Cf* __restrict__ h,
                    const float2* __restrict__ tw, float2* __restrict__ Y,
                    int T, int64_t S, int fir_only)
 {

@@ -30,7 +30,7 @@ FLAG_GENERIC = 2
 EXPORTS = ("ppf_plan_create", "ppf_plan_destroy", "ppf_execute", "ppf_execute_host",
            "ppf_stream_open", "ppf_stream_push", "ppf_stream_position", "ppf_stream_close",
            "ppf_status_string", "ppf_plan_kernel_name", "ppf_launch_count", "ppf_variant_count",
-           "ppf_variant_name")
+           "ppf_variant_name", "ppf_execute_noalloc")
 
 
 class PPFError(RuntimeError):
@@ -69,6 +69,7 @@ def load(path: str | None = None):
             "ppf_launch_count": ([], i64),
             "ppf_variant_count": ([i32, i32, i32], i32),
             "ppf_variant_name": ([i32, i32, i32, i32], ctypes.c_char_p),
+            "ppf_execute_noalloc": ([i32, i32, i32, vp, vp, vp, i64, vp], i32),
         }
         for name, (args, res) in sig.items():
             fn = getattr(lib, name)
@@ -163,6 +164,12 @@ def ppf_variant_count(N: int, T: int, dtype: str = "c32") -> int:
 def ppf_variant_name(N: int, T: int, dtype: str, i: int) -> str | None:
     r = load().ppf_variant_name(int(N), int(T), DTYPES[dtype], int(i))
     return r.decode() if r else None
+
+
+def ppf_execute_noalloc(N: int, T: int, dtype: str, d_h: int, d_in: int, d_out: int, n_spectra: int,
+                        stream: int = 0) -> int:
+    """No-allocation PPF (see include/ppf.h): coefficients as a device FP32 array."""
+    return load().ppf_execute_noalloc(int(N), int(T), DTYPES[dtype], d_h, d_in, d_out, int(n_spectra), stream)
 
 
 def flag_variant(i: int) -> int:
