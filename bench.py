@@ -85,6 +85,29 @@ def peaks():
         return FALLBACK_HBM_GBS, "fallback"
 
 
+def kernel_source_hash() -> str:
+    """sha256 over the CUDA sources and the tuned table (identifies a kernel build)."""
+    import glob
+    import hashlib
+    hh = hashlib.sha256()
+    for f in sorted(glob.glob(os.path.join(ROOT, "paper_1411_3656_gb300", "csrc", "*"))):
+        with open(f, "rb") as fh:
+            hh.update(os.path.basename(f).encode() + fh.read())
+    return hh.hexdigest()
+
+
+def measured_traffic(workload: str, dtype: str):
+    """DRAM bytes per step from the committed ncu summary, if it was taken on this kernel build."""
+    path = os.path.join(ROOT, "profiles", f"traffic_{workload}_{dtype}.txt")
+    try:
+        kv = dict(line.split(":", 1) for line in open(path) if ":" in line and not line.startswith("#"))
+        if kv.get("source_sha256", "").strip() != kernel_source_hash():
+            return None
+        return float(kv["traffic_bytes_per_step"])
+    except Exception:
+        return None
+
+
 def make_input(args, n_samples, dtype):
     """Seeded host input: complex64 stream (or its FP16 / int8 I-Q storage)."""
     from paper_1411_3656_gb300 import synth
@@ -370,7 +393,10 @@ def run_ours(args):
                        "parallelism": f"replicas x{world}"},
             "x_realtime": data_s * args.steps / (elapsed_ms / 1e3),
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s",
-                         "frac": achieved / hbm, "traffic": None,
+                         "frac": achieved / hbm,
+                         "traffic": measured_traffic(args.workload, dtype)
+                         if (not args.cells and args.seconds == 1.0) else None,
+                         "algorithmic_bytes_per_step": tot_bytes,
                          "kernel": "fused FIR+FFT (all cells, byte-weighted)", "peak_source": peak_src},
             "clocks": clock,
             "e2e": e2e,
