@@ -10,26 +10,28 @@
 
 namespace ppf {
 
-int ring_variants_c32_small(int N, int T, int want, KernelEntry* out);
-int ring_variants_c32_large(int N, int T, int want, KernelEntry* out);
-int cluster_variants_c32_a(int N, int T, int want, KernelEntry* out);
-int cluster_variants_c32_b(int N, int T, int want, KernelEntry* out);
+int ring_variants_c32(int N, int T, int want, KernelEntry* out);
+int cluster_variants_c32(int N, int T, int want, KernelEntry* out);
+int ring_variants_c16(int N, int T, int want, KernelEntry* out);
+int cluster_variants_c16(int N, int T, int want, KernelEntry* out);
+int ring_variants_ci8(int N, int T, int want, KernelEntry* out);
+int cluster_variants_ci8(int N, int T, int want, KernelEntry* out);
 
 using VariantFn = int (*)(int, int, int, KernelEntry*);
 
 // Number of variants for (N, T, dtype); fills *out with variant `want` if it exists.
 int variants(int N, int T, int dtype, int want, KernelEntry* out)
 {
-    static const VariantFn c32[] = {ring_variants_c32_small, ring_variants_c32_large, cluster_variants_c32_a,
-                                    cluster_variants_c32_b};
+    static const VariantFn lists[3][2] = {{ring_variants_c32, cluster_variants_c32},
+                                          {ring_variants_c16, cluster_variants_c16},
+                                          {ring_variants_ci8, cluster_variants_ci8}};
+    if (dtype < 0 || dtype > 2) return 0;
     int n = 0;
-    if (dtype == 0) {
-        for (VariantFn f : c32) {
-            KernelEntry e;
-            const int c = f(N, T, want - n, &e);
-            if (want - n >= 0 && want - n < c && out) *out = e;
-            n += c;
-        }
+    for (VariantFn f : lists[dtype]) {
+        KernelEntry e;
+        const int c = f(N, T, want - n, &e);
+        if (want - n >= 0 && want - n < c && out) *out = e;
+        n += c;
     }
     return n;
 }

@@ -208,16 +208,31 @@ def test_full_size_realtime_second_sampled(ppf, N, T):
 VARIANT_CELLS = [(N, T) for N in (128, 256, 512, 1024, 2048, 4096) for T in (4, 8, 16, 32)]
 
 
+def _stored(x, dtype, seed):
+    if dtype == "c16":
+        return synth.to_fp16_iq(x)
+    if dtype == "ci8":
+        return synth.int8_iq(x.shape[0], seed)
+    return x
+
+
 @pytest.mark.parametrize("N,T", VARIANT_CELLS)
-def test_every_variant(ppf, N, T):
-    """Every compiled tile-shape variant of the specialised kernels matches the oracle."""
-    n = ppf.ppf_variant_count(N, T, "c32")
+@pytest.mark.parametrize("dtype", ["c32", "c16", "ci8"])
+def test_every_variant(ppf, N, T, dtype):
+    """Every compiled tile-shape variant of the specialised kernels matches the oracle.
+
+    Reduced-precision inputs are compared with the oracle run on the stored
+    values and the FP16-rounded coefficients the device uses.
+    """
+    n = ppf.ppf_variant_count(N, T, dtype)
     if n == 0:
         pytest.skip("no specialised variant for this size")
     S = max(3, 40960 // N) + 3
     x, h = _rand(N, T, S, 2000 + N + T)
-    ref = oracle.ppf(x, h, N, T, S)
+    xs = _stored(x, dtype, 2100 + N + T)
+    hr = h if dtype == "c32" else h.astype(np.float16).astype(np.float32)
+    ref = oracle.ppf(xs, hr, N, T, S)
     for i in range(n):
-        Y, kern = _run(ppf, x, h, N, T, S, flags=ppf.flag_variant(i))
-        assert kern == ppf.ppf_variant_name(N, T, "c32", i)
+        Y, kern = _run(ppf, xs, h, N, T, S, dtype=dtype, flags=ppf.flag_variant(i))
+        assert kern == ppf.ppf_variant_name(N, T, dtype, i)
         assert synth.rel_l2(Y, ref) <= TOL32, kern
