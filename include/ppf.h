@@ -174,6 +174,46 @@ ppf_status_t ppf_stream_push(ppf_stream_t s, const void* d_chunk, int64_t n_samp
 ppf_status_t ppf_execute_noalloc(int N, int T, ppf_dtype_t dtype, const float* d_h, const void* d_in,
                                  void* d_out, int64_t n_spectra, void* stream);
 
+/*
+ * Batches: many independent streams (each with its own plan, so its own N, T,
+ * dtype and coefficients) in as few launches as possible.  This is the
+ * method's data-parallel form over streams (Section 3 processes one stream;
+ * independent streams simply run side by side).  Jobs whose plans use the
+ * same specialised kernel share one persistent launch over a device work list
+ * of (job, spectrum band) items; jobs on the general kernel launch one by one.
+ */
+typedef struct ppf_batch_s* ppf_batch_t;
+
+typedef struct {
+    ppf_plan_t plan;     /* the job's plan (not owned; must outlive the batch) */
+    const void* d_in;    /* device input, (n_spectra + T - 1) * N samples, 16-byte aligned */
+    void* d_out;         /* device output, n_spectra * N complex64, 16-byte aligned */
+    int64_t n_spectra;   /* spectra of this job, >= 0 */
+} ppf_job_t;
+
+#define PPF_BATCH_GRAPH 1u   /* capture the launches into a CUDA graph on the first execute, replay after */
+
+/*
+ * ppf_batch_create -- group `jobs` by kernel, split them into spectrum bands
+ * and upload the work lists (device memory owned by the batch).  The jobs'
+ * pointers are fixed for the batch's lifetime; their contents may change
+ * between executions.  Synchronises the device.  Errors: PPF_ERR_INVALID_ARG
+ * (null, negative count, bad job), PPF_ERR_MISALIGNED, PPF_ERR_OUT_OF_MEMORY,
+ * PPF_ERR_CUDA.
+ */
+ppf_status_t ppf_batch_create(ppf_batch_t* out, const ppf_job_t* jobs, int n_jobs, unsigned flags);
+
+/* Enqueue every job of the batch on `stream` (cudaStream_t as void*), as a
+ * CUDA graph launch when the batch was created with PPF_BATCH_GRAPH. */
+ppf_status_t ppf_batch_execute(ppf_batch_t batch, void* stream);
+
+/* Kernel launches one execution enqueues (1 for a captured graph counts its
+ * kernels), or -1 for a NULL batch. */
+int ppf_batch_launches(ppf_batch_t batch);
+
+/* Release the batch's device memory and graph.  Synchronises the device. */
+ppf_status_t ppf_batch_destroy(ppf_batch_t batch);
+
 /* Total samples pushed and spectra emitted so far (either pointer may be NULL). */
 ppf_status_t ppf_stream_position(ppf_stream_t s, int64_t* samples_in, int64_t* spectra_out);
 

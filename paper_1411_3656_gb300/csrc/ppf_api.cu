@@ -60,6 +60,22 @@ struct ppf_stream_s {
 };
 
 namespace {
+int sample_bytes(ppf_dtype_t d);
+}
+
+namespace ppf {
+// Plan internals for the batch builder (ppf_batch.cu).
+bool plan_info(ppf_plan_t plan, PlanView* view, KernelEntry* entry, int* bps)
+{
+    if (!plan || (plan->flags & PPF_FLAG_FIR_ONLY)) return false;
+    *view = plan->view;
+    *entry = plan->entry;
+    *bps = sample_bytes(plan->dtype);
+    return true;
+}
+}  // namespace ppf
+
+namespace {
 
 int sample_bytes(ppf_dtype_t d)
 {

@@ -272,12 +272,13 @@ __device__ __forceinline__ void stage2(float2* X, const StageTwiddles<C::N1, C::
 
 template <class C>
 __global__ void __launch_bounds__(C::NT, C::MINB)
-ppf_cluster_kernel(const __grid_constant__ CUtensorMap xmap, const typename C::coef_t* __restrict__ h,
-                   const float2* __restrict__ tw, float2* __restrict__ Y, int64_t S, int* __restrict__ err)
+ppf_cluster_kernel(const __grid_constant__ CUtensorMap xmap, const PpfWork wl, const float2* __restrict__ tw,
+                   int* __restrict__ err)
 {
     constexpr int N = C::N, T = C::T, NT = C::NT, RB = C::RB, NCH = C::NCH, P = C::P;
     constexpr int G = C::G, RBT = C::RBT, BPS = C::BPS, RING_ROWS = C::RING_ROWS, NC = C::NC, C1 = C::C1;
     using PV = typename Pair<typename C::In>::vec;
+    using coef_t = typename C::coef_t;
 
     extern __shared__ __align__(128) unsigned char smem[];
     unsigned char* ring = smem;
@@ -290,14 +291,6 @@ ppf_cluster_kernel(const __grid_constant__ CUtensorMap xmap, const typename C::c
     const int tid = threadIdx.x;
     const int rank = (int)cluster_ctarank();
     const int cid = blockIdx.x / P, ncl = gridDim.x / P;
-    const int64_t nblk = (S + RB - 1) / RB;
-    const int64_t blo = nblk * cid / ncl;
-    const int64_t bhi = nblk * (cid + 1) / ncl;
-    const int nb = (int)(bhi - blo);  // identical for every CTA of the cluster
-    const int64_t s_lo = blo * RB;
-    const int64_t s_hi = S < bhi * RB ? S : bhi * RB;
-    const int64_t in_end = s_hi + T - 1;
-    const int nchunks = nb > 0 ? (int)((in_end - s_lo + RB - 1) / RB) : 0;
 
     if (tid == 0) {
         for (int i = 0; i < NCH; ++i) mbar_init(&bars[i], 1);
@@ -311,38 +304,12 @@ ppf_cluster_kernel(const __grid_constant__ CUtensorMap xmap, const typename C::c
     // before any distributed-memory store or remote arrive
     cluster_arrive_release();
     cluster_wait_acquire();
-
-    uint64_t policy = 0;
-    int issued = 0;
-    auto issue = [&](int k) {
-        uint64_t* bar = &bars[k % NCH];
-        mbar_arrive_expect_tx(bar, (uint32_t)C::CHUNK_BYTES);
-        tma_load_3d(ring + (k % NCH) * C::CHUNK_BYTES, &xmap, rank * C1, 0, (int)(s_lo + (int64_t)k * RB), bar,
-                    policy);
-    };
-    if (tid == 0 && nb > 0) {
-        policy = l2_evict_first_policy();
-        const int first = nchunks < NCH ? nchunks : NCH;
-        for (int k = 0; k < first; ++k) issue(k);
-        issued = first;
-    }
+    const uint64_t policy = l2_evict_first_policy();
 
     // FIR ownership: channel pairs (c1l, c1l+1) at c2 of this CTA's slice
     const int rg = C::PAIRS >= NT ? 0 : tid / C::PAIRS;
     const int pbase = C::PAIRS >= NT ? tid : tid % C::PAIRS;
     const int i0 = rg * RBT;
-    float hr[G][T][2];
-#pragma unroll
-    for (int g = 0; g < G; ++g) {
-        const int pp = pbase + g * NT;
-        const int c1l = 2 * (pp % (C1 / 2)), c2 = pp / (C1 / 2);
-        const int c = rank * C1 + c1l + C::N1 * c2;
-#pragma unroll
-        for (int t = 0; t < T; ++t) {
-            hr[g][t][0] = coef_f(h[t * N + c]);
-            hr[g][t][1] = coef_f(h[t * N + c + 1]);
-        }
-    }
     StageTwiddles<C::N2, C1, NT> tw1;
     tw1.load(tw, N);
     StageTwiddles<C::N1, C::K2, NT> tw2;
@@ -350,102 +317,167 @@ ppf_cluster_kernel(const __grid_constant__ CUtensorMap xmap, const typename C::c
     Stage1Out<C> so;
     so.load(tw, X, xfull, rank);
 
-    int waited = 0, rrb = 0;
+    int cbase = 0;  // ring chunks this CTA issued in earlier bands (slots and phases continue)
+    int gbase = 0;  // blocks this cluster exchanged in earlier bands (X parity and phases continue)
     bool failed = false;
-    // Software pipeline: iteration b filters and sends block b, then finishes
-    // block b-1, whose exchange data arrived while block b was being filtered.
-    for (int b = 0; b <= nb; ++b) {
-        if (b < nb) {
-            bool ok = true;
-            if (!failed) {
-                const int need = (b + C::KO < nchunks ? b + C::KO : nchunks - 1) + 1;
-                for (; waited < need; ++waited) {
-                    if (!mbar_wait_bounded(&bars[waited % NCH], (uint32_t)((waited / NCH) & 1))) {
-                        ok = false;
-                        break;
-                    }
-                }
-            }
-            // A failed wait is recorded and the cluster keeps its schedule (no
-            // early exit, so no CTA waits on one that has left).
-            if (__syncthreads_or(!ok)) failed = true;
+    // Every CTA of a cluster walks the same items, so the cluster keeps one
+    // schedule of exchanges and nobody waits on a peer that has moved on.
+    for (int it = cid;; it += ncl) {
+        PpfJob job;
+        const void* tmap;
+        int64_t blo, bhi;
+        if (wl.items == nullptr) {
+            if (it != cid) break;
+            job = wl.one;
+            tmap = &xmap;
+            const int64_t nblk = (job.S + RB - 1) / RB;
+            blo = nblk * cid / ncl;
+            bhi = nblk * (cid + 1) / ncl;
+        } else {
+            if (it >= wl.n_items) break;
+            const PpfItem item = wl.items[it];
+            job = wl.jobs[item.job];
+            tmap = job.tmap;
+            blo = item.blo;
+            bhi = item.bhi;
+        }
+        if (blo >= bhi) continue;
+        const coef_t* __restrict__ h = static_cast<const coef_t*>(job.h);
+        float2* __restrict__ Y = job.Y;
+        const int64_t S = job.S;
+        const int nb = (int)(bhi - blo);
+        const int64_t s_lo = blo * RB;
+        const int64_t s_hi = S < bhi * RB ? S : bhi * RB;
+        const int64_t in_end = s_hi + T - 1;
+        const int nchunks = (int)((in_end - s_lo + RB - 1) / RB);
 
-            // 1. FIR over the ring
+        int issued = 0;
+        auto issue = [&](int k) {
+            const int slot = (cbase + k) % NCH;
+            mbar_arrive_expect_tx(&bars[slot], (uint32_t)C::CHUNK_BYTES);
+            tma_load_3d(ring + slot * C::CHUNK_BYTES, tmap, rank * C1, 0, (int)(s_lo + (int64_t)k * RB), &bars[slot],
+                        policy);
+        };
+        if (tid == 0 && !failed) {
+            const int first = nchunks < NCH ? nchunks : NCH;
+            for (int k = 0; k < first; ++k) issue(k);
+            issued = first;
+        }
+
+        float hr[G][T][2];
 #pragma unroll
-            for (int g = 0; g < G; ++g) {
-                const int pp = pbase + g * NT;
-                const int l = (pp / (C1 / 2)) * C1 + 2 * (pp % (C1 / 2));
-                float2 a0[RBT], a1[RBT];
+        for (int g = 0; g < G; ++g) {
+            const int pp = pbase + g * NT;
+            const int c1l = 2 * (pp % (C1 / 2)), c2 = pp / (C1 / 2);
+            const int c = rank * C1 + c1l + C::N1 * c2;
 #pragma unroll
-                for (int i = 0; i < RBT; ++i) {
-                    a0[i] = make_float2(0.f, 0.f);
-                    a1[i] = make_float2(0.f, 0.f);
-                }
-#pragma unroll
-                for (int u = 0; u < RBT + T - 1; ++u) {
-                    int rr = rrb + i0 + u;
-                    rr = rr >= RING_ROWS ? rr - RING_ROWS : rr;
-                    const PV pv = *reinterpret_cast<const PV*>(ring + ((size_t)rr * NC + l) * BPS);
-                    float2 v0, v1;
-                    Pair<typename C::In>::split(pv, v0, v1);
-#pragma unroll
-                    for (int i = 0; i < RBT; ++i) {
-                        const int t = u - i;
-                        if (t >= 0 && t < T) {
-                            a0[i].x = fmaf(hr[g][t][0], v0.x, a0[i].x);
-                            a0[i].y = fmaf(hr[g][t][0], v0.y, a0[i].y);
-                            a1[i].x = fmaf(hr[g][t][1], v1.x, a1[i].x);
-                            a1[i].y = fmaf(hr[g][t][1], v1.y, a1[i].y);
+            for (int t = 0; t < T; ++t) {
+                hr[g][t][0] = coef_f(h[t * N + c]);
+                hr[g][t][1] = coef_f(h[t * N + c + 1]);
+            }
+        }
+
+        int waited = 0, rrb = (cbase % NCH) * RB;
+        // Software pipeline: iteration b filters and sends block b, then
+        // finishes block b-1, whose exchange data arrived meanwhile.
+        for (int b = 0; b <= nb; ++b) {
+            if (b < nb) {
+                bool ok = true;
+                if (!failed) {
+                    const int need = (b + C::KO < nchunks ? b + C::KO : nchunks - 1) + 1;
+                    for (; waited < need; ++waited) {
+                        const int gk = cbase + waited;
+                        if (!mbar_wait_bounded(&bars[gk % NCH], (uint32_t)((gk / NCH) & 1))) {
+                            ok = false;
+                            break;
                         }
                     }
                 }
-#pragma unroll
-                for (int i = 0; i < RBT; ++i)
-                    *reinterpret_cast<float4*>(A + (i0 + i) * C::RSB + l) =
-                        make_float4(a0[i].x, a0[i].y, a1[i].x, a1[i].y);
-            }
-            __syncthreads();
-            if (tid == 0 && !failed && issued < nchunks && issued == b + NCH) {
-                issue(issued);
-                ++issued;
-            }
-            rrb += RB;
-            rrb = rrb >= RING_ROWS ? rrb - RING_ROWS : rrb;
+                // A failed wait is recorded and the cluster keeps its schedule (no
+                // early exit, so no CTA waits on one that has left).
+                if (__syncthreads_or(!ok)) failed = true;
 
-            // 2-3. N2-point DFTs, four-step twiddle, send to the owning CTAs
-            const int par = b & 1;
-            if (tid == 0) mbar_arrive_expect_tx(&xfull[par], (uint32_t)C::XBYTES);
-            stage1_upto_last<C>(A, tw1, so);
-            // the owners have finished reading X[par] of block b-2
-            bool okf = true;
-            if (b >= 2 && !failed) okf = mbar_wait_bounded(&xfree[par], (uint32_t)(((b >> 1) - 1) & 1));
-            if (__syncthreads_or(!okf)) failed = true;
-            stage1_pass<C, fft_npass(C::N2) - 1>(A, tw1, so, (uint32_t)(par * C::X_SLOTS * 8),
-                                                 (uint32_t)(par * 8));
-        }
-        if (b >= 1) {
-            // 4. block b-1: once every byte of X[par] is here, N1-point DFTs and store
-            const int bp = b - 1, par = bp & 1;
-            bool okf = true;
-            if (!failed) okf = mbar_wait_bounded(&xfull[par], (uint32_t)((bp >> 1) & 1));
-            if (__syncthreads_or(!okf)) failed = true;
-            const int64_t s0 = s_lo + (int64_t)bp * RB;
-            const int rows = (int)(s_hi - s0 < RB ? s_hi - s0 : RB);
-            stage2<C>(X + par * C::X_SLOTS, tw2, Y + s0 * N, rows, rank, [&] {
-                // every thread's last reads of X[par] have returned; free it for the senders
+                // 1. FIR over the ring
+#pragma unroll
+                for (int g = 0; g < G; ++g) {
+                    const int pp = pbase + g * NT;
+                    const int l = (pp / (C1 / 2)) * C1 + 2 * (pp % (C1 / 2));
+                    float2 a0[RBT], a1[RBT];
+#pragma unroll
+                    for (int i = 0; i < RBT; ++i) {
+                        a0[i] = make_float2(0.f, 0.f);
+                        a1[i] = make_float2(0.f, 0.f);
+                    }
+#pragma unroll
+                    for (int u = 0; u < RBT + T - 1; ++u) {
+                        int rr = rrb + i0 + u;
+                        rr = rr >= RING_ROWS ? rr - RING_ROWS : rr;
+                        const PV pv = *reinterpret_cast<const PV*>(ring + ((size_t)rr * NC + l) * BPS);
+                        float2 v0, v1;
+                        Pair<typename C::In>::split(pv, v0, v1);
+#pragma unroll
+                        for (int i = 0; i < RBT; ++i) {
+                            const int t = u - i;
+                            if (t >= 0 && t < T) {
+                                a0[i].x = fmaf(hr[g][t][0], v0.x, a0[i].x);
+                                a0[i].y = fmaf(hr[g][t][0], v0.y, a0[i].y);
+                                a1[i].x = fmaf(hr[g][t][1], v1.x, a1[i].x);
+                                a1[i].y = fmaf(hr[g][t][1], v1.y, a1[i].y);
+                            }
+                        }
+                    }
+#pragma unroll
+                    for (int i = 0; i < RBT; ++i)
+                        *reinterpret_cast<float4*>(A + (i0 + i) * C::RSB + l) =
+                            make_float4(a0[i].x, a0[i].y, a1[i].x, a1[i].y);
+                }
                 __syncthreads();
-                if (tid < P) mbar_arrive_remote(map_shared_rank(smem_u32(&xfree[par]), (uint32_t)tid));
-            });
+                if (tid == 0 && !failed && issued < nchunks && issued == b + NCH) {
+                    issue(issued);
+                    ++issued;
+                }
+                rrb += RB;
+                rrb = rrb >= RING_ROWS ? rrb - RING_ROWS : rrb;
+
+                // 2-3. N2-point DFTs, four-step twiddle, send to the owning CTAs
+                const int gb = gbase + b, par = gb & 1;
+                if (tid == 0) mbar_arrive_expect_tx(&xfull[par], (uint32_t)C::XBYTES);
+                stage1_upto_last<C>(A, tw1, so);
+                // the owners have finished reading X[par] of exchange gb-2
+                bool okf = true;
+                if (gb >= 2 && !failed) okf = mbar_wait_bounded(&xfree[par], (uint32_t)(((gb >> 1) - 1) & 1));
+                if (__syncthreads_or(!okf)) failed = true;
+                stage1_pass<C, fft_npass(C::N2) - 1>(A, tw1, so, (uint32_t)(par * C::X_SLOTS * 8),
+                                                     (uint32_t)(par * 8));
+            }
+            if (b >= 1) {
+                // 4. block b-1: once every byte of X[par] is here, N1-point DFTs and store
+                const int bp = b - 1, gb = gbase + bp, par = gb & 1;
+                bool okf = true;
+                if (!failed) okf = mbar_wait_bounded(&xfull[par], (uint32_t)((gb >> 1) & 1));
+                if (__syncthreads_or(!okf)) failed = true;
+                const int64_t s0 = s_lo + (int64_t)bp * RB;
+                const int rows = (int)(s_hi - s0 < RB ? s_hi - s0 : RB);
+                stage2<C>(X + par * C::X_SLOTS, tw2, Y + s0 * N, rows, rank, [&] {
+                    // every thread's last reads of X[par] have returned; free it for the senders
+                    __syncthreads();
+                    if (tid < P) mbar_arrive_remote(map_shared_rank(smem_u32(&xfree[par]), (uint32_t)tid));
+                });
+            }
         }
+        if (failed && tid == 0) {
+            for (int k = waited; k < issued; ++k) {
+                const int gk = cbase + k;
+                mbar_wait_bounded(&bars[gk % NCH], (uint32_t)((gk / NCH) & 1), kWaitLimitNs / 4);
+            }
+        }
+        cbase += nchunks;
+        gbase += nb;
     }
     // no CTA leaves while a peer may still store into its shared memory
     cluster_arrive_release();
     cluster_wait_acquire();
-    if (failed && tid == 0) {
-        for (int k = waited; k < issued; ++k)
-            mbar_wait_bounded(&bars[k % NCH], (uint32_t)((k / NCH) & 1), kWaitLimitNs / 4);
-        atomicExch(err, 1);
-    }
+    if (failed && tid == 0) atomicExch(err, 1);
 }
 
 }  // namespace ppf

@@ -6,6 +6,7 @@
 #include <cudaTypedefs.h>
 
 #include <cstdio>
+#include <cstring>
 #include <mutex>
 
 #include "ppf_cluster.cuh"
@@ -90,13 +91,37 @@ cudaError_t launch_cluster(const PlanView& p, const void* in, float2* out, int64
     if (ncl <= 0) return cudaSuccess;
     CUtensorMap m;
     if (!encode_input_map<C>(&m, in, S + C::T - 1)) return cudaErrorInvalidValue;
+    PpfWork w{};
+    w.one.x = in;
+    w.one.Y = out;
+    w.one.h = p.h;
+    w.one.S = S;
     cudaLaunchAttribute attr[1];
     cudaLaunchConfig_t cfg = launch_config<C>(ncl * C::P, st, attr);
-    cudaError_t e = cudaLaunchKernelEx(&cfg, ppf_cluster_kernel<C>, m,
-                                       static_cast<const typename C::coef_t*>(p.h), p.tw, out, S, p.err);
+    cudaError_t e = cudaLaunchKernelEx(&cfg, ppf_cluster_kernel<C>, m, w, p.tw, p.err);
     note_launch();
     if (e != cudaSuccess) return e;
     return cudaGetLastError();
+}
+
+template <class C>
+cudaError_t launch_cluster_work(const PlanView& p, const PpfWork& w, int grid, cudaStream_t st)
+{
+    if (grid <= 0) return cudaSuccess;
+    CUtensorMap unused;
+    std::memset(&unused, 0, sizeof(unused));
+    cudaLaunchAttribute attr[1];
+    cudaLaunchConfig_t cfg = launch_config<C>(grid, st, attr);
+    cudaError_t e = cudaLaunchKernelEx(&cfg, ppf_cluster_kernel<C>, unused, w, p.tw, p.err);
+    note_launch();
+    if (e != cudaSuccess) return e;
+    return cudaGetLastError();
+}
+
+template <class C>
+bool encode_job_map(void* tmap128, const void* x, int64_t rows)
+{
+    return encode_input_map<C>(static_cast<CUtensorMap*>(tmap128), x, rows);
 }
 
 template <class C>
@@ -109,6 +134,10 @@ KernelEntry entry()
     e.name = name;
     e.prepare = prepare_cluster<C>;
     e.launch = launch_cluster<C>;
+    e.launch_work = launch_cluster_work<C>;
+    e.encode = encode_job_map<C>;
+    e.rows_per_block = C::RB;
+    e.cluster = C::P;
     return e;
 }
 

@@ -167,6 +167,34 @@ template <> struct Coef<InC32> { using type = float; };
 __device__ __forceinline__ float coef_f(float v) { return v; }
 __device__ __forceinline__ float coef_f(__half v) { return __half2float(v); }
 
+// ------------------------------------------------------------------ work lists
+// One job of a launch: a contiguous input stream (S + T - 1 rows of N samples),
+// its S output spectra and its coefficients (each stream may have its own h).
+// `tmap` is the job's input tensor map in global memory (cluster kernel only).
+struct PpfJob {
+    const void* x;
+    float2* Y;
+    const void* h;
+    const void* tmap;
+    int64_t S;
+};
+// A work item: blocks [blo, bhi) of job `job` (a block is the kernel's RB spectra).
+struct PpfItem {
+    int job;
+    int pad;
+    int64_t blo;
+    int64_t bhi;
+};
+// Where a launch's work comes from.  With items == nullptr the launch has the
+// one job `one`, split into equal contiguous bands over the grid; otherwise
+// CTA (or cluster) i processes items i, i + grid, i + 2*grid, ...
+struct PpfWork {
+    PpfJob one;
+    const PpfJob* jobs;
+    const PpfItem* items;
+    int n_items;
+};
+
 // ------------------------------------------------------------------ FFT plan
 // Radix of pass p for a length-N row: 16 first (or N itself when N <= 16),
 // then 16s, the remainder last.  Every pass after the first has Ns >= 16.

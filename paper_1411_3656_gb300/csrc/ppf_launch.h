@@ -4,6 +4,8 @@
 #include <cuda_runtime.h>
 #include <cstdint>
 
+#include "ppf_device.cuh"
+
 namespace ppf {
 
 // What a launcher needs to know about a plan (plain data, no ownership).
@@ -20,11 +22,20 @@ struct PlanView {
 using PrepareFn = cudaError_t (*)(PlanView&);
 using LaunchFn = cudaError_t (*)(const PlanView&, const void* in, float2* out, int64_t S,
                                  cudaStream_t stream);
+// One launch over a device work list (items/jobs in device memory); `grid`
+// CTAs (a multiple of the cluster size).
+using LaunchWorkFn = cudaError_t (*)(const PlanView&, const PpfWork& work, int grid, cudaStream_t stream);
+// Encode a job's input tensor map (cluster kernels); 128 bytes.
+using EncodeFn = bool (*)(void* tmap128, const void* x, int64_t rows);
 
 struct KernelEntry {
     const char* name = nullptr;
     PrepareFn prepare = nullptr;
     LaunchFn launch = nullptr;
+    LaunchWorkFn launch_work = nullptr;  // null: no work-list form (general kernel)
+    EncodeFn encode = nullptr;           // null: jobs need no tensor map
+    int rows_per_block = 0;              // spectra per block (RB)
+    int cluster = 1;                     // CTAs per cluster
 };
 
 // General kernel for (N, dtype); runtime T.  Defined in ppf_generic.cu.

@@ -96,12 +96,13 @@ __device__ __forceinline__ void fft_rows_pp(float2* a, float2* b, const PassTwid
 
 template <class C>
 __global__ void __launch_bounds__(C::NT, C::MINB)
-ppf_ring_kernel(const typename C::raw* __restrict__ x, const typename C::coef_t* __restrict__ h,
-                const float2* __restrict__ tw, float2* __restrict__ Y, int64_t S, int* __restrict__ err)
+ppf_ring_kernel(const PpfWork wl, const float2* __restrict__ tw, int* __restrict__ err)
 {
     constexpr int N = C::N, T = C::T, NT = C::NT, RB = C::RB, NCH = C::NCH, RS = C::RS;
     constexpr int G = C::G, RBT = C::RBT, BPS = C::BPS, RING_ROWS = C::RING_ROWS;
     using PV = typename Pair<typename C::In>::vec;
+    using raw = typename C::raw;
+    using coef_t = typename C::coef_t;
 
     extern __shared__ __align__(128) unsigned char smem[];
     unsigned char* ring = smem;
@@ -110,127 +111,158 @@ ppf_ring_kernel(const typename C::raw* __restrict__ x, const typename C::coef_t*
     uint64_t* bars = reinterpret_cast<uint64_t*>(smem + C::RING_BYTES + C::FFT_BYTES);
 
     const int tid = threadIdx.x;
-    const int64_t nblk = (S + RB - 1) / RB;
-    const int64_t blo = nblk * blockIdx.x / gridDim.x;
-    const int64_t bhi = nblk * (blockIdx.x + 1) / gridDim.x;
-    if (blo >= bhi) return;
-    const int nb = (int)(bhi - blo);
-    const int64_t s_lo = blo * RB;
-    const int64_t s_hi = S < bhi * RB ? S : bhi * RB;
-    const int64_t in_end = s_hi + T - 1;  // input rows the band reads: [s_lo, in_end)
-    const int nchunks = (int)((in_end - s_lo + RB - 1) / RB);
-
-    uint64_t policy = 0;
     if (tid == 0) {
         for (int i = 0; i < NCH; ++i) mbar_init(&bars[i], 1);
         fence_mbar_init();
     }
     __syncthreads();
-    int issued = 0;  // chunks issued so far (meaningful in thread 0)
-    auto issue = [&](int k) {
-        const int64_t r0 = s_lo + (int64_t)k * RB;
-        const int64_t rows = in_end - r0 < RB ? in_end - r0 : RB;
-        const uint32_t bytes = (uint32_t)(rows * N * BPS);
-        uint64_t* bar = &bars[k % NCH];
-        mbar_arrive_expect_tx(bar, bytes);
-        tma_load_1d(ring + (k % NCH) * C::CHUNK_BYTES, x + r0 * N, bytes, bar, policy);
-    };
-    if (tid == 0) {
-        policy = l2_evict_first_policy();
-        const int first = nchunks < NCH ? nchunks : NCH;
-        for (int k = 0; k < first; ++k) issue(k);
-        issued = first;
-    }
+    const uint64_t policy = l2_evict_first_policy();
 
-    // Thread -> (row group, channel pairs); coefficients of its channels in registers.
+    // Thread -> (row group, channel pairs).
     const int rg = C::PAIRS >= NT ? 0 : tid / C::PAIRS;
     const int pbase = C::PAIRS >= NT ? tid : tid % C::PAIRS;
     const int i0 = rg * RBT;
-    float hr[G][T][2];
-#pragma unroll
-    for (int g = 0; g < G; ++g) {
-        const int c = 2 * (pbase + g * NT);
-#pragma unroll
-        for (int t = 0; t < T; ++t) {
-            hr[g][t][0] = coef_f(h[t * N + c]);
-            hr[g][t][1] = coef_f(h[t * N + c + 1]);
-        }
-    }
-
     PassTwiddles<N, NT> twr;
     twr.load(tw);
 
-    int waited = 0;  // chunks every thread has waited for
-    int rrb = 0;     // ring row of the block's first input row
-    bool failed = false;
-    for (int b = 0; b < nb; ++b) {
-        // 1. the block needs chunks b .. b+KO
-        bool ok = true;
-        const int need = (b + C::KO < nchunks ? b + C::KO : nchunks - 1) + 1;
-        for (; waited < need; ++waited) {
-            if (!mbar_wait_bounded(&bars[waited % NCH], (uint32_t)((waited / NCH) & 1))) {
-                ok = false;
-                break;
-            }
+    // Chunks this CTA issued in earlier bands: ring slots and mbarrier phases
+    // continue across bands (every chunk of a band is waited for in that band).
+    int cbase = 0;
+    for (int it = blockIdx.x;; it += gridDim.x) {
+        PpfJob job;
+        int64_t blo, bhi;
+        if (wl.items == nullptr) {
+            if (it != (int)blockIdx.x) break;
+            job = wl.one;
+            const int64_t nblk = (job.S + RB - 1) / RB;
+            blo = nblk * blockIdx.x / gridDim.x;
+            bhi = nblk * (blockIdx.x + 1) / gridDim.x;
+        } else {
+            if (it >= wl.n_items) break;
+            const PpfItem item = wl.items[it];
+            job = wl.jobs[item.job];
+            blo = item.blo;
+            bhi = item.bhi;
         }
-        if (__syncthreads_or(!ok)) {
-            failed = true;
-            break;
+        if (blo >= bhi) continue;
+        const raw* __restrict__ x = static_cast<const raw*>(job.x);
+        const coef_t* __restrict__ h = static_cast<const coef_t*>(job.h);
+        float2* __restrict__ Y = job.Y;
+        const int64_t S = job.S;
+        const int nb = (int)(bhi - blo);
+        const int64_t s_lo = blo * RB;
+        const int64_t s_hi = S < bhi * RB ? S : bhi * RB;
+        const int64_t in_end = s_hi + T - 1;  // input rows the band reads: [s_lo, in_end)
+        const int nchunks = (int)((in_end - s_lo + RB - 1) / RB);
+
+        int issued = 0;  // chunks of this band issued so far (meaningful in thread 0)
+        auto issue = [&](int k) {
+            const int64_t r0 = s_lo + (int64_t)k * RB;
+            const int64_t rows = in_end - r0 < RB ? in_end - r0 : RB;
+            const uint32_t bytes = (uint32_t)(rows * N * BPS);
+            const int slot = (cbase + k) % NCH;
+            mbar_arrive_expect_tx(&bars[slot], bytes);
+            tma_load_1d(ring + slot * C::CHUNK_BYTES, x + r0 * N, bytes, &bars[slot], policy);
+        };
+        if (tid == 0) {
+            const int first = nchunks < NCH ? nchunks : NCH;
+            for (int k = 0; k < first; ++k) issue(k);
+            issued = first;
         }
 
-        // 2. FIR over the ring (Eq. 1), RBT spectra x 2 channels per pair
+        // coefficients of this thread's channels, in FP32 registers
+        float hr[G][T][2];
 #pragma unroll
         for (int g = 0; g < G; ++g) {
             const int c = 2 * (pbase + g * NT);
-            float2 a0[RBT], a1[RBT];
 #pragma unroll
-            for (int i = 0; i < RBT; ++i) {
-                a0[i] = make_float2(0.f, 0.f);
-                a1[i] = make_float2(0.f, 0.f);
+            for (int t = 0; t < T; ++t) {
+                hr[g][t][0] = coef_f(h[t * N + c]);
+                hr[g][t][1] = coef_f(h[t * N + c + 1]);
             }
-#pragma unroll
-            for (int u = 0; u < RBT + T - 1; ++u) {
-                int rr = rrb + i0 + u;
-                rr = rr >= RING_ROWS ? rr - RING_ROWS : rr;
-                const PV pv = *reinterpret_cast<const PV*>(ring + ((size_t)rr * N + c) * BPS);
-                float2 v0, v1;
-                Pair<typename C::In>::split(pv, v0, v1);
-#pragma unroll
-                for (int i = 0; i < RBT; ++i) {
-                    const int t = u - i;
-                    if (t >= 0 && t < T) {
-                        a0[i].x = fmaf(hr[g][t][0], v0.x, a0[i].x);
-                        a0[i].y = fmaf(hr[g][t][0], v0.y, a0[i].y);
-                        a1[i].x = fmaf(hr[g][t][1], v1.x, a1[i].x);
-                        a1[i].y = fmaf(hr[g][t][1], v1.y, a1[i].y);
-                    }
+        }
+
+        int waited = 0;                    // chunks of this band every thread has waited for
+        int rrb = (cbase % NCH) * RB;      // ring row of the block's first input row
+        bool failed = false;
+        for (int b = 0; b < nb; ++b) {
+            // 1. the block needs chunks b .. b+KO
+            bool ok = true;
+            const int need = (b + C::KO < nchunks ? b + C::KO : nchunks - 1) + 1;
+            for (; waited < need; ++waited) {
+                const int gk = cbase + waited;
+                if (!mbar_wait_bounded(&bars[gk % NCH], (uint32_t)((gk / NCH) & 1))) {
+                    ok = false;
+                    break;
                 }
             }
+            if (__syncthreads_or(!ok)) {
+                failed = true;
+                break;
+            }
+
+            // 2. FIR over the ring (Eq. 1), RBT spectra x 2 channels per pair
 #pragma unroll
-            for (int i = 0; i < RBT; ++i)
-                *reinterpret_cast<float4*>(bufA + (i0 + i) * RS + c) = make_float4(a0[i].x, a0[i].y, a1[i].x, a1[i].y);
-        }
-        __syncthreads();
+            for (int g = 0; g < G; ++g) {
+                const int c = 2 * (pbase + g * NT);
+                float2 a0[RBT], a1[RBT];
+#pragma unroll
+                for (int i = 0; i < RBT; ++i) {
+                    a0[i] = make_float2(0.f, 0.f);
+                    a1[i] = make_float2(0.f, 0.f);
+                }
+#pragma unroll
+                for (int u = 0; u < RBT + T - 1; ++u) {
+                    int rr = rrb + i0 + u;
+                    rr = rr >= RING_ROWS ? rr - RING_ROWS : rr;
+                    const PV pv = *reinterpret_cast<const PV*>(ring + ((size_t)rr * N + c) * BPS);
+                    float2 v0, v1;
+                    Pair<typename C::In>::split(pv, v0, v1);
+#pragma unroll
+                    for (int i = 0; i < RBT; ++i) {
+                        const int t = u - i;
+                        if (t >= 0 && t < T) {
+                            a0[i].x = fmaf(hr[g][t][0], v0.x, a0[i].x);
+                            a0[i].y = fmaf(hr[g][t][0], v0.y, a0[i].y);
+                            a1[i].x = fmaf(hr[g][t][1], v1.x, a1[i].x);
+                            a1[i].y = fmaf(hr[g][t][1], v1.y, a1[i].y);
+                        }
+                    }
+                }
+#pragma unroll
+                for (int i = 0; i < RBT; ++i)
+                    *reinterpret_cast<float4*>(bufA + (i0 + i) * RS + c) =
+                        make_float4(a0[i].x, a0[i].y, a1[i].x, a1[i].y);
+            }
+            __syncthreads();
 
-        // 3. chunk b is no longer needed: refill its slot
-        if (tid == 0 && issued < nchunks && issued == b + NCH) {
-            issue(issued);
-            ++issued;
-        }
-        rrb += RB;
-        rrb = rrb >= RING_ROWS ? rrb - RING_ROWS : rrb;
+            // 3. chunk b is no longer needed: refill its slot
+            if (tid == 0 && issued < nchunks && issued == b + NCH) {
+                issue(issued);
+                ++issued;
+            }
+            rrb += RB;
+            rrb = rrb >= RING_ROWS ? rrb - RING_ROWS : rrb;
 
-        // 4. FFT of the RB rows; the last pass stores the spectra
-        const int64_t s0 = s_lo + (int64_t)b * RB;
-        const int rows = (int)(s_hi - s0 < RB ? s_hi - s0 : RB);
-        fft_rows_pp<N, RB, NT>(bufA, bufB, twr, Y + s0 * N, rows);
-    }
-    if (failed) {
-        if (tid == 0) {
-            // let the copies still in flight land before the CTA exits
-            for (int k = waited; k < issued; ++k) mbar_wait_bounded(&bars[k % NCH], (uint32_t)((k / NCH) & 1), kWaitLimitNs / 4);
-            atomicExch(err, 1);
+            // 4. FFT of the RB rows; the last pass stores the spectra
+            const int64_t s0 = s_lo + (int64_t)b * RB;
+            const int rows = (int)(s_hi - s0 < RB ? s_hi - s0 : RB);
+            fft_rows_pp<N, RB, NT>(bufA, bufB, twr, Y + s0 * N, rows);
         }
+        if (failed) {
+            if (tid == 0) {
+                // let the copies still in flight land before the CTA exits
+                for (int k = waited; k < issued; ++k) {
+                    const int gk = cbase + k;
+                    mbar_wait_bounded(&bars[gk % NCH], (uint32_t)((gk / NCH) & 1), kWaitLimitNs / 4);
+                }
+                atomicExch(err, 1);
+            }
+            return;
+        }
+        cbase += nchunks;
+        // the FFT of the band's last block may still be reading bufA/bufB and the
+        // next band's FIR writes bufA: the next block's wait barrier orders them
     }
 }
 

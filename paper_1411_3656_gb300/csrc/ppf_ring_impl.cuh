@@ -29,9 +29,21 @@ cudaError_t launch_ring(const PlanView& p, const void* in, float2* out, int64_t 
     const int64_t nblk = (S + C::RB - 1) / C::RB;
     const int grid = (int)(nblk < p.grid_cap ? nblk : p.grid_cap);
     if (grid <= 0) return cudaSuccess;
-    ppf_ring_kernel<C><<<grid, C::NT, C::SMEM, st>>>(static_cast<const typename C::raw*>(in),
-                                                      static_cast<const typename C::coef_t*>(p.h), p.tw, out, S,
-                                                      p.err);
+    PpfWork w{};
+    w.one.x = in;
+    w.one.Y = out;
+    w.one.h = p.h;
+    w.one.S = S;
+    ppf_ring_kernel<C><<<grid, C::NT, C::SMEM, st>>>(w, p.tw, p.err);
+    note_launch();
+    return cudaGetLastError();
+}
+
+template <class C>
+cudaError_t launch_ring_work(const PlanView& p, const PpfWork& w, int grid, cudaStream_t st)
+{
+    if (grid <= 0) return cudaSuccess;
+    ppf_ring_kernel<C><<<grid, C::NT, C::SMEM, st>>>(w, p.tw, p.err);
     note_launch();
     return cudaGetLastError();
 }
@@ -45,6 +57,9 @@ KernelEntry entry()
     e.name = name;
     e.prepare = prepare_ring<C>;
     e.launch = launch_ring<C>;
+    e.launch_work = launch_ring_work<C>;
+    e.rows_per_block = C::RB;
+    e.cluster = 1;
     return e;
 }
 

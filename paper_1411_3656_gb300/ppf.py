@@ -30,7 +30,17 @@ FLAG_GENERIC = 2
 EXPORTS = ("ppf_plan_create", "ppf_plan_destroy", "ppf_execute", "ppf_execute_host",
            "ppf_stream_open", "ppf_stream_push", "ppf_stream_position", "ppf_stream_close",
            "ppf_status_string", "ppf_plan_kernel_name", "ppf_launch_count", "ppf_variant_count",
-           "ppf_variant_name", "ppf_execute_noalloc")
+           "ppf_variant_name", "ppf_execute_noalloc", "ppf_batch_create", "ppf_batch_execute",
+           "ppf_batch_launches", "ppf_batch_destroy")
+
+
+class PPFJob(ctypes.Structure):
+    """ppf_job_t: one stream of a batch."""
+    _fields_ = [("plan", ctypes.c_void_p), ("d_in", ctypes.c_void_p), ("d_out", ctypes.c_void_p),
+                ("n_spectra", ctypes.c_int64)]
+
+
+BATCH_GRAPH = 1
 
 
 class PPFError(RuntimeError):
@@ -70,6 +80,10 @@ def load(path: str | None = None):
             "ppf_variant_count": ([i32, i32, i32], i32),
             "ppf_variant_name": ([i32, i32, i32, i32], ctypes.c_char_p),
             "ppf_execute_noalloc": ([i32, i32, i32, vp, vp, vp, i64, vp], i32),
+            "ppf_batch_create": ([ctypes.POINTER(vp), ctypes.POINTER(PPFJob), i32, ctypes.c_uint], i32),
+            "ppf_batch_execute": ([vp, vp], i32),
+            "ppf_batch_launches": ([vp], i32),
+            "ppf_batch_destroy": ([vp], i32),
         }
         for name, (args, res) in sig.items():
             fn = getattr(lib, name)
@@ -283,6 +297,44 @@ class Stream:
     def close(self):
         if self.handle:
             ppf_stream_close(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class Batch:
+    """Many independent streams (jobs) launched together; see ppf_batch_create.
+
+    ``jobs`` is a list of (Plan, input tensor, output tensor, n_spectra).  The
+    tensors must stay alive (and at the same addresses) as long as the batch.
+    """
+
+    def __init__(self, jobs, graph: bool = False):
+        self._keep = list(jobs)
+        arr = (PPFJob * max(1, len(jobs)))()
+        for i, (plan, x, y, n) in enumerate(jobs):
+            arr[i] = PPFJob(plan.handle, x.data_ptr(), y.data_ptr(), int(n))
+        out = ctypes.c_void_p()
+        _check(load().ppf_batch_create(ctypes.byref(out), arr, len(jobs), BATCH_GRAPH if graph else 0),
+               "ppf_batch_create")
+        self.handle = out.value
+
+    @property
+    def launches(self) -> int:
+        return int(load().ppf_batch_launches(self.handle))
+
+    def execute(self, stream=None):
+        _check(load().ppf_batch_execute(self.handle, _stream_ptr(stream)), "ppf_batch_execute")
+
+    __call__ = execute
+
+    def close(self):
+        if self.handle:
+            _check(load().ppf_batch_destroy(self.handle), "ppf_batch_destroy")
             self.handle = None
 
     def __del__(self):

@@ -1,0 +1,97 @@
+"""Batches of independent streams (ppf_batch_*) against one ppf_execute per stream."""
+import numpy as np
+import pytest
+
+from paper_1411_3656_gb300 import synth
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def ppf():
+    import torch
+    from paper_1411_3656_gb300 import build, ppf as mod
+    build.build()
+    mod.load()
+    assert torch.cuda.is_available()
+    return mod
+
+
+def _jobs(ppf, specs, seed):
+    """specs: (N, T, dtype, S).  Each job gets its own seeded input and h."""
+    import torch
+    out = []
+    for i, (N, T, dt, S) in enumerate(specs):
+        g = np.random.default_rng(seed + i)
+        h = g.standard_normal(N * T).astype(np.float32)
+        x = synth.stream(synth.samples_for(S, N, T), N, seed + 100 + i)
+        if dt == "c16":
+            x = synth.to_fp16_iq(x)
+        elif dt == "ci8":
+            x = synth.int8_iq(synth.samples_for(S, N, T), seed + 200 + i)
+        plan = ppf.Plan(N, T, h, dt)
+        xd = torch.from_numpy(np.ascontiguousarray(x)).cuda()
+        yd = torch.full((S, N), float("nan"), dtype=torch.complex64, device="cuda")
+        out.append((plan, xd, yd, S))
+    return out
+
+
+SPECS = [(256, 8, "c32", 700), (256, 8, "c32", 1500), (1024, 8, "c32", 333), (4096, 16, "c32", 41),
+         (4096, 16, "c32", 9), (2048, 32, "c32", 17), (64, 5, "c32", 90), (128, 4, "c32", 257),
+         (1024, 16, "c16", 120), (512, 8, "ci8", 77), (256, 4, "c32", 0), (2048, 8, "c32", 1)]
+
+
+@pytest.mark.parametrize("graph", [False, True])
+def test_batch_equals_individual(ppf, graph):
+    import torch
+    jobs = _jobs(ppf, SPECS, 5000)
+    batch = ppf.Batch(jobs, graph=graph)
+    kernels = {p.kernel for p, _, _, _ in jobs}
+    assert any(k.startswith("ring") for k in kernels) and any(k.startswith("cluster") for k in kernels)
+    before = ppf.ppf_launch_count()
+    batch.execute()
+    torch.cuda.synchronize()
+    if not graph:
+        assert ppf.ppf_launch_count() - before == batch.launches
+    for plan, xd, yd, S in jobs:
+        ref = plan(xd, n_spectra=S)
+        torch.cuda.synchronize()
+        assert torch.equal(yd, ref), plan.kernel
+    # the batch reads the inputs afresh each time (graph replay included)
+    for plan, xd, yd, S in jobs:
+        if xd.dtype == torch.complex64:
+            xd.mul_(2)
+    batch.execute()
+    torch.cuda.synchronize()
+    for plan, xd, yd, S in jobs:
+        assert torch.equal(yd, plan(xd, n_spectra=S)), plan.kernel
+    batch.close()
+
+
+def test_batch_many_streams_in_few_launches(ppf):
+    """64 streams of six shapes: one launch per specialised kernel, not per stream."""
+    import torch
+    g = np.random.default_rng(77)
+    shapes = [(256, 8), (512, 4), (1024, 8), (2048, 8), (4096, 4), (128, 16)]
+    specs = [(*shapes[i % len(shapes)], "c32", int(g.integers(10, 200))) for i in range(64)]
+    jobs = _jobs(ppf, specs, 9000)
+    batch = ppf.Batch(jobs)
+    assert batch.launches <= len({p.kernel + str((p.N, p.T)) for p, _, _, _ in jobs})
+    batch.execute()
+    torch.cuda.synchronize()
+    for plan, xd, yd, S in jobs:
+        assert torch.equal(yd, plan(xd, n_spectra=S))
+
+
+def test_batch_argument_errors(ppf):
+    import ctypes
+    lib = ppf.load()
+    out = ctypes.c_void_p()
+    assert lib.ppf_batch_create(None, None, 0, 0) == 1
+    assert lib.ppf_batch_create(ctypes.byref(out), None, -1, 0) == 1
+    assert lib.ppf_batch_create(ctypes.byref(out), None, 0, 8) == 1
+    assert lib.ppf_batch_create(ctypes.byref(out), None, 0, 0) == 0
+    assert lib.ppf_batch_launches(out.value) == 0
+    assert lib.ppf_batch_execute(out.value, None) == 0
+    assert lib.ppf_batch_destroy(out.value) == 0
+    assert lib.ppf_batch_execute(None, None) == 1
