@@ -39,6 +39,7 @@
 #ifndef PPF_H_
 #define PPF_H_
 
+#include <stddef.h>
 #include <stdint.h>
 
 #ifdef __cplusplus
@@ -213,6 +214,58 @@ int ppf_batch_launches(ppf_batch_t batch);
 
 /* Release the batch's device memory and graph.  Synchronises the device. */
 ppf_status_t ppf_batch_destroy(ppf_batch_t batch);
+
+/*
+ * Serving: many continuous streams (each a stream of Section 3's real-time
+ * workload, with its own plan) share the GPU.  Streams are admitted while
+ * device memory allows; chunks are queued as they arrive and each tick runs
+ * everything queued so far as one set of launches (continuous batching):
+ * one batched copy of the new chunks behind each stream's FIR history, one
+ * persistent PPF launch per specialised kernel, one batched history carry.
+ * Results are identical to ppf_stream_push on each stream alone.  A server is
+ * not thread-safe; all ticks of a server must be ordered on one CUDA stream.
+ */
+typedef struct ppf_server_s* ppf_server_t;
+
+/* max_streams slots; memory_budget_bytes caps the device memory streams may
+ * reserve (admission also needs that much free device memory). */
+ppf_status_t ppf_server_create(ppf_server_t* out, int max_streams, size_t memory_budget_bytes);
+
+/*
+ * ppf_server_admit -- reserve a slot for a stream with `plan` whose chunks hold
+ * at most max_chunk_samples samples: two device buffers of
+ * T*N + 4*max_chunk_samples + 2*N samples (history plus queued chunks).
+ * *slot_out receives the slot.  PPF_ERR_OUT_OF_MEMORY when the budget or the
+ * free device memory is exhausted, PPF_ERR_BUSY when every slot is taken.
+ */
+ppf_status_t ppf_server_admit(ppf_server_t s, ppf_plan_t plan, int64_t max_chunk_samples, int* slot_out);
+
+/* Free a slot (no chunk may be queued: PPF_ERR_BUSY).  Synchronises the device. */
+ppf_status_t ppf_server_release(ppf_server_t s, int slot);
+
+/*
+ * ppf_server_submit -- queue n_samples (<= max_chunk_samples) new samples of
+ * the slot's stream at d_chunk (device, read during the next tick; keep it
+ * valid until the tick's work completes).  The spectra this chunk completes
+ * are written to d_out (capacity out_capacity_spectra rows, 16-byte aligned)
+ * by the next tick.  PPF_ERR_INVALID_ARG if the capacity is too small,
+ * PPF_ERR_BUSY if the slot's buffer is full (tick first).
+ */
+ppf_status_t ppf_server_submit(ppf_server_t s, int slot, const void* d_chunk, int64_t n_samples, void* d_out,
+                               int64_t out_capacity_spectra);
+
+/* Run one tick on `stream`: every queued chunk of every slot.  *n_done gets the
+ * number of chunks processed (may be NULL).  Returns after enqueuing. */
+ppf_status_t ppf_server_tick(ppf_server_t s, void* stream, int* n_done);
+
+/* Samples submitted and spectra produced (through the last tick) of a slot. */
+ppf_status_t ppf_server_position(ppf_server_t s, int slot, int64_t* samples_in, int64_t* spectra_out);
+
+/* Device bytes reserved, admitted streams, launches of the last tick (any may be NULL). */
+ppf_status_t ppf_server_info(ppf_server_t s, size_t* reserved_bytes, int* streams, int* last_tick_launches);
+
+/* Release every slot and the staging buffers.  Synchronises the device. */
+ppf_status_t ppf_server_destroy(ppf_server_t s);
 
 /* Total samples pushed and spectra emitted so far (either pointer may be NULL). */
 ppf_status_t ppf_stream_position(ppf_stream_t s, int64_t* samples_in, int64_t* spectra_out);

@@ -1,0 +1,472 @@
+// Serving loop core: many continuous streams admitted by device memory,
+// their chunks batched into one set of launches per tick (see include/ppf.h).
+//
+// Per stream the server owns two device buffers (ping-pong) of capacity
+// (T-1)*N + N + max_chunk samples holding the FIR history (Section 2: each
+// output needs the newest sample and T-1 past samples of its channel) plus
+// newly arrived samples.  A tick
+//   1. copies every queued chunk behind its stream's history (one batched
+//      copy launch for all streams),
+//   2. runs the PPF on every stream's newly complete spectra (one persistent
+//      work-list launch per specialised kernel, as in ppf_batch),
+//   3. copies each stream's new history to the front of its other buffer
+//      (one batched copy launch) and swaps the buffers.
+// The per-tick tables (copies, jobs, items, tensor maps) are written into a
+// pinned staging buffer and uploaded with one asynchronous copy; two staging
+// slots alternate so the host can build tick k+1 while tick k runs.
+#include "ppf.h"
+#include "ppf_launch.h"
+
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cstdint>
+#include <cstring>
+#include <map>
+#include <new>
+#include <string>
+#include <vector>
+
+namespace ppf {
+bool plan_info(ppf_plan_t plan, PlanView* view, KernelEntry* entry, int* sample_bytes);
+}
+
+namespace {
+
+// One contiguous device-to-device copy piece (at most kSeg bytes).
+struct CopySeg {
+    const unsigned char* src;
+    unsigned char* dst;
+    int64_t bytes;
+};
+constexpr int64_t kSeg = 64 * 1024;
+
+// Batched copy: CTA i copies segments i, i + grid, ...; 16-byte vectors when
+// both ends are 16-byte aligned, else 4-, 2- or 1-byte elements.
+__global__ void __launch_bounds__(256) batched_copy(const CopySeg* __restrict__ segs, int n)
+{
+    for (int s = blockIdx.x; s < n; s += gridDim.x) {
+        const CopySeg c = segs[s];
+        const uintptr_t a = reinterpret_cast<uintptr_t>(c.src) | reinterpret_cast<uintptr_t>(c.dst);
+        if ((a & 15u) == 0 && (c.bytes & 15) == 0) {
+            const int64_t n16 = c.bytes / 16;
+            const uint4* src = reinterpret_cast<const uint4*>(c.src);
+            uint4* dst = reinterpret_cast<uint4*>(c.dst);
+            for (int64_t i = threadIdx.x; i < n16; i += blockDim.x) dst[i] = __ldcs(src + i);
+        } else if ((a & 3u) == 0 && (c.bytes & 3) == 0) {
+            const int64_t n4 = c.bytes / 4;
+            const uint32_t* src = reinterpret_cast<const uint32_t*>(c.src);
+            uint32_t* dst = reinterpret_cast<uint32_t*>(c.dst);
+            for (int64_t i = threadIdx.x; i < n4; i += blockDim.x) dst[i] = src[i];
+        } else {
+            for (int64_t i = threadIdx.x; i < c.bytes; i += blockDim.x) c.dst[i] = c.src[i];
+        }
+    }
+}
+
+ppf_status_t from_cuda(cudaError_t e)
+{
+    if (e == cudaSuccess) return PPF_OK;
+    if (e == cudaErrorMemoryAllocation) return PPF_ERR_OUT_OF_MEMORY;
+    return PPF_ERR_CUDA;
+}
+
+}  // namespace
+
+struct ppf_server_s {
+    struct Sub {
+        const void* chunk;
+        int64_t n;
+        void* out;
+        int64_t cap;
+    };
+    struct Slot {
+        bool used = false;
+        ppf_plan_t plan = nullptr;
+        ppf::PlanView view;
+        ppf::KernelEntry entry;
+        int bps = 0;
+        unsigned char* buf[2] = {nullptr, nullptr};
+        int64_t cap = 0;       // samples per buffer
+        int cur = 0;
+        int64_t held = 0;      // samples in buf[cur]
+        int64_t base = 0;      // stream index of buf[cur][0]
+        int64_t pushed = 0;
+        int64_t emitted = 0;
+        int64_t max_chunk = 0;
+        size_t bytes = 0;      // device bytes reserved by the slot
+        std::vector<Sub> queue;
+        std::vector<int64_t> done;  // spectra written per submission of the last tick
+    };
+    std::vector<Slot> slots;
+    size_t budget = 0;
+    size_t reserved = 0;
+    int sms = 0;
+    // staging: two pinned host slots + their device mirrors
+    unsigned char* host_stage[2] = {nullptr, nullptr};
+    unsigned char* dev_stage[2] = {nullptr, nullptr};
+    size_t stage_cap = 0;
+    cudaEvent_t stage_free[2] = {nullptr, nullptr};
+    int stage_idx = 0;
+    int64_t ticks = 0;
+    int last_launches = 0;
+};
+
+namespace {
+
+ppf_status_t grow_stage(ppf_server_s* s, size_t need)
+{
+    if (need <= s->stage_cap) return PPF_OK;
+    cudaError_t e = cudaDeviceSynchronize();
+    if (e != cudaSuccess) return from_cuda(e);
+    size_t cap = s->stage_cap ? s->stage_cap : (1 << 20);
+    while (cap < need) cap *= 2;
+    for (int i = 0; i < 2; ++i) {
+        if (s->host_stage[i]) cudaFreeHost(s->host_stage[i]);
+        if (s->dev_stage[i]) cudaFree(s->dev_stage[i]);
+        s->host_stage[i] = nullptr;
+        s->dev_stage[i] = nullptr;
+    }
+    s->stage_cap = 0;
+    for (int i = 0; i < 2; ++i) {
+        e = cudaHostAlloc(reinterpret_cast<void**>(&s->host_stage[i]), cap, cudaHostAllocDefault);
+        if (e == cudaSuccess) e = cudaMalloc(reinterpret_cast<void**>(&s->dev_stage[i]), cap);
+        if (e != cudaSuccess) return from_cuda(e);
+    }
+    s->stage_cap = cap;
+    return PPF_OK;
+}
+
+void add_copy(std::vector<CopySeg>& segs, const void* src, void* dst, int64_t bytes)
+{
+    const unsigned char* s = static_cast<const unsigned char*>(src);
+    unsigned char* d = static_cast<unsigned char*>(dst);
+    for (int64_t off = 0; off < bytes; off += kSeg)
+        segs.push_back({s + off, d + off, std::min(kSeg, bytes - off)});
+}
+
+}  // namespace
+
+extern "C" {
+
+ppf_status_t ppf_server_create(ppf_server_t* out, int max_streams, size_t memory_budget_bytes)
+{
+    if (!out || max_streams < 1 || max_streams > 65536) return PPF_ERR_INVALID_ARG;
+    *out = nullptr;
+    ppf_server_s* s = new (std::nothrow) ppf_server_s();
+    if (!s) return PPF_ERR_OUT_OF_MEMORY;
+    s->slots.resize(max_streams);
+    s->budget = memory_budget_bytes;
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&s->sms, cudaDevAttrMultiProcessorCount, dev);
+    for (int i = 0; i < 2 && e == cudaSuccess; ++i) e = cudaEventCreateWithFlags(&s->stage_free[i], cudaEventDisableTiming);
+    if (e != cudaSuccess) {
+        delete s;
+        return from_cuda(e);
+    }
+    *out = s;
+    return PPF_OK;
+}
+
+ppf_status_t ppf_server_admit(ppf_server_t s, ppf_plan_t plan, int64_t max_chunk_samples, int* slot_out)
+{
+    if (!s || !plan || !slot_out || max_chunk_samples < 1) return PPF_ERR_INVALID_ARG;
+    *slot_out = -1;
+    ppf::PlanView v;
+    ppf::KernelEntry e;
+    int bps = 0;
+    if (!ppf::plan_info(plan, &v, &e, &bps)) return PPF_ERR_INVALID_ARG;
+    int free_slot = -1;
+    for (size_t i = 0; i < s->slots.size(); ++i)
+        if (!s->slots[i].used) {
+            free_slot = (int)i;
+            break;
+        }
+    if (free_slot < 0) return PPF_ERR_BUSY;
+    // Two buffers: history ((T-1)*N + N - 1 samples at most) plus several chunks
+    // queued in one tick; rows rounded so every row start is 16-byte aligned.
+    const int64_t cap = ((int64_t)v.T * v.N + 4 * max_chunk_samples + 2 * v.N);
+    const size_t bytes = 2 * (size_t)cap * bps;
+    size_t free_b = 0, total_b = 0;
+    cudaError_t ce = cudaMemGetInfo(&free_b, &total_b);
+    if (ce != cudaSuccess) return from_cuda(ce);
+    if (s->reserved + bytes > s->budget || bytes + (64u << 20) > free_b) return PPF_ERR_OUT_OF_MEMORY;
+    ppf_server_s::Slot& sl = s->slots[free_slot];
+    for (int i = 0; i < 2; ++i) {
+        ce = cudaMalloc(reinterpret_cast<void**>(&sl.buf[i]), (size_t)cap * bps);
+        if (ce != cudaSuccess) {
+            if (sl.buf[0]) cudaFree(sl.buf[0]);
+            sl.buf[0] = sl.buf[1] = nullptr;
+            return from_cuda(ce);
+        }
+    }
+    sl.used = true;
+    sl.plan = plan;
+    sl.view = v;
+    sl.entry = e;
+    sl.bps = bps;
+    sl.cap = cap;
+    sl.cur = 0;
+    sl.held = sl.base = sl.pushed = sl.emitted = 0;
+    sl.max_chunk = max_chunk_samples;
+    sl.bytes = bytes;
+    sl.queue.clear();
+    sl.done.clear();
+    s->reserved += bytes;
+    *slot_out = free_slot;
+    return PPF_OK;
+}
+
+ppf_status_t ppf_server_release(ppf_server_t s, int slot)
+{
+    if (!s || slot < 0 || slot >= (int)s->slots.size() || !s->slots[slot].used) return PPF_ERR_INVALID_ARG;
+    ppf_server_s::Slot& sl = s->slots[slot];
+    if (!sl.queue.empty()) return PPF_ERR_BUSY;
+    cudaError_t e = cudaDeviceSynchronize();
+    for (int i = 0; i < 2; ++i)
+        if (sl.buf[i]) cudaFree(sl.buf[i]);
+    s->reserved -= sl.bytes;
+    sl = ppf_server_s::Slot();
+    return from_cuda(e);
+}
+
+ppf_status_t ppf_server_submit(ppf_server_t s, int slot, const void* d_chunk, int64_t n_samples, void* d_out,
+                               int64_t out_capacity_spectra)
+{
+    if (!s || slot < 0 || slot >= (int)s->slots.size() || !s->slots[slot].used) return PPF_ERR_INVALID_ARG;
+    ppf_server_s::Slot& sl = s->slots[slot];
+    if (n_samples < 0 || n_samples > sl.max_chunk || (n_samples > 0 && !d_chunk) || out_capacity_spectra < 0)
+        return PPF_ERR_INVALID_ARG;
+    int64_t queued = 0;
+    for (auto& q : sl.queue) queued += q.n;
+    if (sl.held + queued + n_samples > sl.cap) return PPF_ERR_BUSY;  // tick first
+    // spectra this submission completes
+    const int64_t N = sl.view.N, T = sl.view.T;
+    const int64_t before = std::max<int64_t>(0, (sl.pushed + queued) / N - T + 1);
+    const int64_t after = std::max<int64_t>(0, (sl.pushed + queued + n_samples) / N - T + 1);
+    if (after - before > out_capacity_spectra) return PPF_ERR_INVALID_ARG;
+    if (after > before && (!d_out || (reinterpret_cast<uintptr_t>(d_out) & 15u))) return PPF_ERR_MISALIGNED;
+    sl.queue.push_back({d_chunk, n_samples, d_out, out_capacity_spectra});
+    return PPF_OK;
+}
+
+ppf_status_t ppf_server_tick(ppf_server_t s, void* stream, int* n_done)
+{
+    if (!s) return PPF_ERR_INVALID_ARG;
+    if (n_done) *n_done = 0;
+    if (cudaPeekAtLastError() != cudaSuccess) return PPF_ERR_CUDA;
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+
+    // 1. host bookkeeping: gather copies, PPF jobs, carry copies
+    std::vector<CopySeg> gather, carry;
+    struct G {
+        ppf::PlanView view;
+        ppf::KernelEntry entry;
+        std::vector<ppf::PpfJob> jobs;
+        std::vector<std::vector<unsigned char>> maps;
+    };
+    std::map<std::string, G> groups;
+    std::vector<std::string> order;
+    struct Single {
+        ppf::PlanView view;
+        ppf::KernelEntry entry;
+        const void* in;
+        float2* out;
+        int64_t S;
+    };
+    std::vector<Single> singles;
+    int processed = 0;
+    for (auto& sl : s->slots) {
+        if (!sl.used || sl.queue.empty()) continue;
+        const int64_t N = sl.view.N, T = sl.view.T;
+        unsigned char* cur = sl.buf[sl.cur];
+        sl.done.assign(sl.queue.size(), 0);
+        for (size_t qi = 0; qi < sl.queue.size(); ++qi) {
+            const auto& q = sl.queue[qi];
+            if (q.n > 0) add_copy(gather, q.chunk, cur + sl.held * sl.bps, q.n * sl.bps);
+            sl.held += q.n;
+            sl.pushed += q.n;
+            const int64_t complete = std::max<int64_t>(0, sl.pushed / N - T + 1);
+            const int64_t fresh = complete - sl.emitted;
+            if (fresh > 0) {
+                const void* in = cur + (sl.emitted * N - sl.base) * sl.bps;
+                float2* out = static_cast<float2*>(q.out);
+                if (sl.entry.launch_work) {
+                    char key[160];
+                    std::snprintf(key, sizeof(key), "%d:%d:%d:%s", sl.view.N, sl.view.T, sl.view.dtype, sl.entry.name);
+                    auto it = groups.find(key);
+                    if (it == groups.end()) {
+                        groups[key] = G{sl.view, sl.entry, {}, {}};
+                        order.push_back(key);
+                        it = groups.find(key);
+                    }
+                    ppf::PpfJob j{};
+                    j.x = in;
+                    j.Y = out;
+                    j.h = sl.view.h;
+                    j.S = fresh;
+                    if (sl.entry.encode) {
+                        std::vector<unsigned char> m(128, 0);
+                        if (!sl.entry.encode(m.data(), in, fresh + T - 1)) return PPF_ERR_INVALID_ARG;
+                        it->second.maps.push_back(std::move(m));
+                    }
+                    it->second.jobs.push_back(j);
+                } else {
+                    singles.push_back({sl.view, sl.entry, in, out, fresh});
+                }
+                sl.done[qi] = fresh;
+                sl.emitted = complete;
+            }
+            ++processed;
+        }
+        // new history: from the first row of the next spectrum to the end
+        const int64_t drop = sl.emitted * N - sl.base;
+        const int64_t keep = sl.held - drop;
+        unsigned char* other = sl.buf[sl.cur ^ 1];
+        if (keep > 0) add_copy(carry, cur + drop * sl.bps, other, keep * sl.bps);
+        sl.cur ^= 1;
+        sl.base += drop;
+        sl.held = keep;
+        sl.queue.clear();
+    }
+    if (processed == 0) return PPF_OK;
+
+    // 2. items for each group (about one per resident CTA or cluster)
+    struct Tab {
+        size_t maps_at, jobs_at, items_at;
+        std::vector<ppf::PpfItem> items;
+        int grid;
+    };
+    std::vector<Tab> tabs(order.size());
+    size_t off = 0;
+    auto place = [&](size_t n, size_t align) {
+        off = (off + align - 1) / align * align;
+        const size_t at = off;
+        off += n;
+        return at;
+    };
+    const size_t gather_at = place(sizeof(CopySeg) * gather.size(), 16);
+    const size_t carry_at = place(sizeof(CopySeg) * carry.size(), 16);
+    for (size_t gi = 0; gi < order.size(); ++gi) {
+        G& g = groups[order[gi]];
+        Tab& tb = tabs[gi];
+        const int RB = g.entry.rows_per_block;
+        const int units = std::max(1, g.view.grid_cap / g.entry.cluster);
+        int64_t total = 0;
+        for (auto& j : g.jobs) total += (j.S + RB - 1) / RB;
+        const int64_t target = std::max<int64_t>(1, (total + units - 1) / units);
+        for (size_t ji = 0; ji < g.jobs.size(); ++ji) {
+            const int64_t nblk = (g.jobs[ji].S + RB - 1) / RB;
+            const int64_t pieces = std::max<int64_t>(1, (nblk + target / 2) / target);
+            for (int64_t k = 0; k < pieces; ++k) {
+                ppf::PpfItem it{};
+                it.job = (int)ji;
+                it.blo = nblk * k / pieces;
+                it.bhi = nblk * (k + 1) / pieces;
+                if (it.bhi > it.blo) tb.items.push_back(it);
+            }
+        }
+        tb.grid = std::min<int>(units, (int)tb.items.size()) * g.entry.cluster;
+        tb.maps_at = place(128 * g.maps.size(), 128);
+        tb.jobs_at = place(sizeof(ppf::PpfJob) * g.jobs.size(), 16);
+        tb.items_at = place(sizeof(ppf::PpfItem) * tb.items.size(), 16);
+    }
+    ppf_status_t ps = grow_stage(s, off + 256);
+    if (ps != PPF_OK) return ps;
+
+    // 3. fill the staging slot (after the tick that last used it has uploaded it)
+    const int k = s->stage_idx;
+    s->stage_idx ^= 1;
+    cudaError_t e = cudaEventSynchronize(s->stage_free[k]);
+    if (e != cudaSuccess) return from_cuda(e);
+    unsigned char* hs = s->host_stage[k];
+    unsigned char* ds = s->dev_stage[k];
+    std::memcpy(hs + gather_at, gather.data(), sizeof(CopySeg) * gather.size());
+    std::memcpy(hs + carry_at, carry.data(), sizeof(CopySeg) * carry.size());
+    std::vector<ppf::PpfWork> works(order.size());
+    for (size_t gi = 0; gi < order.size(); ++gi) {
+        G& g = groups[order[gi]];
+        Tab& tb = tabs[gi];
+        for (size_t m = 0; m < g.maps.size(); ++m) {
+            std::memcpy(hs + tb.maps_at + 128 * m, g.maps[m].data(), 128);
+            g.jobs[m].tmap = ds + tb.maps_at + 128 * m;
+        }
+        std::memcpy(hs + tb.jobs_at, g.jobs.data(), sizeof(ppf::PpfJob) * g.jobs.size());
+        std::memcpy(hs + tb.items_at, tb.items.data(), sizeof(ppf::PpfItem) * tb.items.size());
+        works[gi].jobs = reinterpret_cast<const ppf::PpfJob*>(ds + tb.jobs_at);
+        works[gi].items = reinterpret_cast<const ppf::PpfItem*>(ds + tb.items_at);
+        works[gi].n_items = (int)tb.items.size();
+    }
+    e = cudaMemcpyAsync(ds, hs, off, cudaMemcpyHostToDevice, st);
+    if (e == cudaSuccess) e = cudaEventRecord(s->stage_free[k], st);
+    if (e != cudaSuccess) return from_cuda(e);
+
+    // 4. launches: gather, PPF groups, general-kernel jobs, carry
+    int launches = 0;
+    const int cgrid = std::max(1, std::min<int>((int)gather.size(), 4 * s->sms));
+    if (!gather.empty()) {
+        batched_copy<<<cgrid, 256, 0, st>>>(reinterpret_cast<const CopySeg*>(ds + gather_at), (int)gather.size());
+        ppf::note_launch();
+        ++launches;
+    }
+    for (size_t gi = 0; gi < order.size() && e == cudaSuccess; ++gi) {
+        G& g = groups[order[gi]];
+        e = g.entry.launch_work(g.view, works[gi], tabs[gi].grid, st);
+        ++launches;
+    }
+    for (auto& sg : singles) {
+        if (e != cudaSuccess) break;
+        e = sg.entry.launch(sg.view, sg.in, sg.out, sg.S, st);
+        ++launches;
+    }
+    if (e == cudaSuccess && !carry.empty()) {
+        const int kgrid = std::max(1, std::min<int>((int)carry.size(), 4 * s->sms));
+        batched_copy<<<kgrid, 256, 0, st>>>(reinterpret_cast<const CopySeg*>(ds + carry_at), (int)carry.size());
+        ppf::note_launch();
+        ++launches;
+        e = cudaGetLastError();
+    }
+    if (e != cudaSuccess) return from_cuda(e);
+    s->last_launches = launches;
+    ++s->ticks;
+    if (n_done) *n_done = processed;
+    return PPF_OK;
+}
+
+ppf_status_t ppf_server_position(ppf_server_t s, int slot, int64_t* samples_in, int64_t* spectra_out)
+{
+    if (!s || slot < 0 || slot >= (int)s->slots.size() || !s->slots[slot].used) return PPF_ERR_INVALID_ARG;
+    if (samples_in) *samples_in = s->slots[slot].pushed;
+    if (spectra_out) *spectra_out = s->slots[slot].emitted;
+    return PPF_OK;
+}
+
+ppf_status_t ppf_server_info(ppf_server_t s, size_t* reserved_bytes, int* streams, int* last_tick_launches)
+{
+    if (!s) return PPF_ERR_INVALID_ARG;
+    int n = 0;
+    for (auto& sl : s->slots) n += sl.used ? 1 : 0;
+    if (reserved_bytes) *reserved_bytes = s->reserved;
+    if (streams) *streams = n;
+    if (last_tick_launches) *last_tick_launches = s->last_launches;
+    return PPF_OK;
+}
+
+ppf_status_t ppf_server_destroy(ppf_server_t s)
+{
+    if (!s) return PPF_ERR_INVALID_ARG;
+    cudaError_t e = cudaDeviceSynchronize();
+    for (auto& sl : s->slots)
+        for (int i = 0; i < 2; ++i)
+            if (sl.buf[i]) cudaFree(sl.buf[i]);
+    for (int i = 0; i < 2; ++i) {
+        if (s->host_stage[i]) cudaFreeHost(s->host_stage[i]);
+        if (s->dev_stage[i]) cudaFree(s->dev_stage[i]);
+        if (s->stage_free[i]) cudaEventDestroy(s->stage_free[i]);
+    }
+    delete s;
+    return from_cuda(e);
+}
+
+}  // extern "C"

@@ -31,7 +31,9 @@ EXPORTS = ("ppf_plan_create", "ppf_plan_destroy", "ppf_execute", "ppf_execute_ho
            "ppf_stream_open", "ppf_stream_push", "ppf_stream_position", "ppf_stream_close",
            "ppf_status_string", "ppf_plan_kernel_name", "ppf_launch_count", "ppf_variant_count",
            "ppf_variant_name", "ppf_execute_noalloc", "ppf_batch_create", "ppf_batch_execute",
-           "ppf_batch_launches", "ppf_batch_destroy")
+           "ppf_batch_launches", "ppf_batch_destroy", "ppf_server_create", "ppf_server_admit",
+           "ppf_server_release", "ppf_server_submit", "ppf_server_tick", "ppf_server_position",
+           "ppf_server_info", "ppf_server_destroy")
 
 
 class PPFJob(ctypes.Structure):
@@ -84,6 +86,14 @@ def load(path: str | None = None):
             "ppf_batch_execute": ([vp, vp], i32),
             "ppf_batch_launches": ([vp], i32),
             "ppf_batch_destroy": ([vp], i32),
+            "ppf_server_create": ([ctypes.POINTER(vp), i32, ctypes.c_size_t], i32),
+            "ppf_server_admit": ([vp, vp, i64, ctypes.POINTER(i32)], i32),
+            "ppf_server_release": ([vp, i32], i32),
+            "ppf_server_submit": ([vp, i32, vp, i64, vp, i64], i32),
+            "ppf_server_tick": ([vp, vp, ctypes.POINTER(i32)], i32),
+            "ppf_server_position": ([vp, i32, ctypes.POINTER(i64), ctypes.POINTER(i64)], i32),
+            "ppf_server_info": ([vp, ctypes.POINTER(ctypes.c_size_t), ctypes.POINTER(i32), ctypes.POINTER(i32)], i32),
+            "ppf_server_destroy": ([vp], i32),
         }
         for name, (args, res) in sig.items():
             fn = getattr(lib, name)
@@ -335,6 +345,72 @@ class Batch:
     def close(self):
         if self.handle:
             _check(load().ppf_batch_destroy(self.handle), "ppf_batch_destroy")
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class Server:
+    """Continuous batching of many streams on one GPU (ppf_server_*)."""
+
+    def __init__(self, max_streams: int, memory_budget_bytes: int):
+        out = ctypes.c_void_p()
+        _check(load().ppf_server_create(ctypes.byref(out), int(max_streams), int(memory_budget_bytes)),
+               "ppf_server_create")
+        self.handle = out.value
+        self.plans = {}
+
+    def admit(self, plan: Plan, max_chunk_samples: int) -> int:
+        """Slot id, or raises PPFError (PPF_ERR_OUT_OF_MEMORY / PPF_ERR_BUSY) when refused."""
+        slot = ctypes.c_int(-1)
+        _check(load().ppf_server_admit(self.handle, plan.handle, int(max_chunk_samples), ctypes.byref(slot)),
+               "ppf_server_admit")
+        self.plans[slot.value] = plan
+        return slot.value
+
+    def release(self, slot: int):
+        _check(load().ppf_server_release(self.handle, int(slot)), "ppf_server_release")
+        self.plans.pop(slot, None)
+
+    def expected(self, slot: int, queued: int, n: int) -> int:
+        """Spectra a chunk of n samples completes, after `queued` samples already queued."""
+        plan = self.plans[slot]
+        pushed, _ = self.position(slot)
+        a = max(0, (pushed + queued) // plan.N - plan.T + 1)
+        b = max(0, (pushed + queued + n) // plan.N - plan.T + 1)
+        return b - a
+
+    def submit(self, slot: int, chunk, out, n_samples: int | None = None) -> int:
+        n = n_samples_of(chunk) if n_samples is None else int(n_samples)
+        cap = out.numel() // self.plans[slot].N if out is not None else 0
+        st = load().ppf_server_submit(self.handle, int(slot), chunk.data_ptr() if n else None, n,
+                                      out.data_ptr() if (out is not None and out.numel()) else None, cap)
+        return st
+
+    def tick(self, stream=None) -> int:
+        n = ctypes.c_int(0)
+        _check(load().ppf_server_tick(self.handle, _stream_ptr(stream), ctypes.byref(n)), "ppf_server_tick")
+        return n.value
+
+    def position(self, slot: int):
+        a, b = ctypes.c_int64(0), ctypes.c_int64(0)
+        _check(load().ppf_server_position(self.handle, int(slot), ctypes.byref(a), ctypes.byref(b)),
+               "ppf_server_position")
+        return a.value, b.value
+
+    def info(self):
+        r, n, l = ctypes.c_size_t(0), ctypes.c_int(0), ctypes.c_int(0)
+        _check(load().ppf_server_info(self.handle, ctypes.byref(r), ctypes.byref(n), ctypes.byref(l)),
+               "ppf_server_info")
+        return {"reserved_bytes": r.value, "streams": n.value, "last_tick_launches": l.value}
+
+    def close(self):
+        if self.handle:
+            _check(load().ppf_server_destroy(self.handle), "ppf_server_destroy")
             self.handle = None
 
     def __del__(self):

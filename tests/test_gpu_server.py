@@ -1,0 +1,156 @@
+"""Serving (ppf_server_*): continuous batching of many streams.
+
+The defining property: a stream's spectra are the same alone and in the mix
+(bitwise: every spectrum is computed by the same kernel from the same inputs),
+and equal to ppf_execute on the stream's concatenated samples.
+"""
+import numpy as np
+import pytest
+
+from paper_1411_3656_gb300 import synth
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def ppf():
+    import torch
+    from paper_1411_3656_gb300 import build, ppf as mod
+    build.build()
+    mod.load()
+    assert torch.cuda.is_available()
+    return mod
+
+
+class Feed:
+    """A stream: plan, its whole sample sequence on the device, cut into chunks."""
+
+    def __init__(self, ppf, N, T, dtype, total, seed, chunks):
+        import torch
+        g = np.random.default_rng(seed)
+        self.h = g.standard_normal(N * T).astype(np.float32)
+        x = synth.stream(total, N, seed + 1)
+        if dtype == "ci8":
+            x = synth.int8_iq(total, seed + 2)
+        elif dtype == "c16":
+            x = synth.to_fp16_iq(x)
+        self.plan = ppf.Plan(N, T, self.h, dtype)
+        self.x = torch.from_numpy(np.ascontiguousarray(x)).cuda()
+        self.N, self.T, self.dtype, self.total = N, T, dtype, total
+        cuts = np.sort(g.choice(np.arange(1, total), size=chunks - 1, replace=False))
+        self.bounds = list(zip([0, *cuts], [*cuts, total]))
+        self.outs = []
+
+    def chunk(self, i):
+        a, b = self.bounds[i]
+        return self.x[a:b]
+
+    def batch_reference(self):
+        return self.plan(self.x)
+
+
+def _serve(ppf, feeds, schedule, max_chunk):
+    """schedule: list of ticks, each a list of (feed index, chunk index)."""
+    import torch
+    srv = ppf.Server(max_streams=16, memory_budget_bytes=8 << 30)
+    slots = [srv.admit(f.plan, max_chunk) for f in feeds]
+    outs = [[] for _ in feeds]
+    keep = []
+    for tick in schedule:
+        queued = [0] * len(feeds)
+        for fi, ci in tick:
+            f = feeds[fi]
+            c = f.chunk(ci)
+            n = c.shape[0]
+            k = srv.expected(slots[fi], queued[fi], n)
+            out = torch.empty((k, f.N), dtype=torch.complex64, device="cuda")
+            assert srv.submit(slots[fi], c, out) == 0
+            queued[fi] += n
+            outs[fi].append(out)
+            keep.append(c)
+        srv.tick()
+    torch.cuda.synchronize()
+    res = [torch.cat(o) if o else None for o in outs]
+    srv.close()
+    return res
+
+
+def test_alone_equals_mix_equals_batch(ppf):
+    import torch
+    rng = np.random.default_rng(3)
+    A = Feed(ppf, 1024, 8, "c32", 1024 * 300 + 77, 11, 23)
+    others = [Feed(ppf, 256, 16, "c32", 256 * 900 + 5, 21, 17), Feed(ppf, 4096, 16, "c32", 4096 * 60 + 999, 31, 9),
+              Feed(ppf, 512, 4, "ci8", 512 * 500 + 3, 41, 13), Feed(ppf, 2048, 8, "c16", 2048 * 100 + 1, 51, 11),
+              Feed(ppf, 64, 3, "c32", 64 * 700, 61, 7)]
+    max_chunk = max(b - a for f in [A, *others] for a, b in f.bounds)
+    # alone: A's chunks, one or two per tick
+    sched_alone, i = [], 0
+    while i < len(A.bounds):
+        k = 1 + int(rng.integers(0, 2))
+        sched_alone.append([(0, j) for j in range(i, min(i + k, len(A.bounds)))])
+        i += k
+    alone = _serve(ppf, [A], sched_alone, max_chunk)[0]
+    # mix: every stream's chunks interleaved at random over ticks
+    feeds = [A, *others]
+    nxt = [0] * len(feeds)
+    sched_mix = []
+    while any(nxt[f] < len(feeds[f].bounds) for f in range(len(feeds))):
+        tick = []
+        for f in range(len(feeds)):
+            k = int(rng.integers(0, 3))
+            for _ in range(k):
+                if nxt[f] < len(feeds[f].bounds):
+                    tick.append((f, nxt[f]))
+                    nxt[f] += 1
+        sched_mix.append(tick)
+    mixed = _serve(ppf, feeds, sched_mix, max_chunk)
+    torch.cuda.synchronize()
+    assert torch.equal(alone, mixed[0])
+    for f, got in zip(feeds, mixed):
+        ref = f.batch_reference()
+        torch.cuda.synchronize()
+        assert got.shape == ref.shape
+        assert torch.equal(got, ref), (f.N, f.T, f.dtype)
+
+
+def test_admission_by_memory_and_slots(ppf):
+    N, T = 1024, 8
+    h = np.ones(N * T, np.float32)
+    plan = ppf.Plan(N, T, h)
+    chunk = 1 << 20
+    per_slot = 2 * (T * N + 4 * chunk + 2 * N) * 8
+    srv = ppf.Server(max_streams=3, memory_budget_bytes=2 * per_slot + 100)
+    a = srv.admit(plan, chunk)
+    b = srv.admit(plan, chunk)
+    with pytest.raises(ppf.PPFError) as e:
+        srv.admit(plan, chunk)
+    assert e.value.status == 4  # PPF_ERR_OUT_OF_MEMORY: budget exhausted
+    srv.release(a)
+    c = srv.admit(plan, chunk)
+    assert srv.info()["streams"] == 2
+    srv.close()
+    srv = ppf.Server(max_streams=1, memory_budget_bytes=1 << 40)
+    srv.admit(plan, 1024)
+    with pytest.raises(ppf.PPFError) as e:
+        srv.admit(plan, 1024)
+    assert e.value.status == 7  # PPF_ERR_BUSY: no free slot
+    srv.close()
+
+
+def test_submit_errors(ppf):
+    import torch
+    N, T = 256, 4
+    plan = ppf.Plan(N, T, np.ones(N * T, np.float32))
+    srv = ppf.Server(max_streams=2, memory_budget_bytes=1 << 30)
+    s = srv.admit(plan, 4 * N)
+    x = torch.zeros(8 * N, dtype=torch.complex64, device="cuda")
+    small = torch.empty((0, N), dtype=torch.complex64, device="cuda")
+    assert srv.submit(s, x[:8 * N], small, 8 * N) == 1          # more than max_chunk
+    assert srv.submit(s, x[:4 * N], small, 4 * N) == 1          # completes 1 spectrum, no room
+    out = torch.empty((1, N), dtype=torch.complex64, device="cuda")
+    assert srv.submit(s, x[:4 * N], out, 4 * N) == 0
+    with pytest.raises(ppf.PPFError):
+        srv.release(s)                                          # chunk still queued
+    assert srv.tick() == 1
+    srv.release(s)
+    srv.close()
