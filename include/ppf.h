@@ -234,7 +234,8 @@ ppf_status_t ppf_server_create(ppf_server_t* out, int max_streams, size_t memory
 /*
  * ppf_server_admit -- reserve a slot for a stream with `plan` whose chunks hold
  * at most max_chunk_samples samples: two device buffers of
- * T*N + 4*max_chunk_samples + 2*N samples (history plus queued chunks).
+ * 8*T*N + 4*max_chunk_samples + 2*N samples (history and boundary regions
+ * for up to four chunks queued between ticks).
  * *slot_out receives the slot.  PPF_ERR_OUT_OF_MEMORY when the budget or the
  * free device memory is exhausted, PPF_ERR_BUSY when every slot is taken.
  */
@@ -248,11 +249,19 @@ ppf_status_t ppf_server_release(ppf_server_t s, int slot);
  * the slot's stream at d_chunk (device, read during the next tick; keep it
  * valid until the tick's work completes).  The spectra this chunk completes
  * are written to d_out (capacity out_capacity_spectra rows, 16-byte aligned)
- * by the next tick.  PPF_ERR_INVALID_ARG if the capacity is too small,
- * PPF_ERR_BUSY if the slot's buffer is full (tick first).
+ * by the next tick.  Spectra whose windows lie inside the chunk are read from
+ * d_chunk in place when it is 16-byte aligned at their first row.
+ * PPF_ERR_INVALID_ARG if the capacity is too small, PPF_ERR_BUSY if four
+ * chunks are already queued for the slot (tick first).
  */
 ppf_status_t ppf_server_submit(ppf_server_t s, int slot, const void* d_chunk, int64_t n_samples, void* d_out,
                                int64_t out_capacity_spectra);
+
+/* Submit n chunks at once (arrays of n entries, meanings as in
+ * ppf_server_submit); statuses[i] (may be NULL) gets each one's status.
+ * Returns PPF_OK when all were queued, else PPF_ERR_BUSY (see statuses). */
+ppf_status_t ppf_server_submit_many(ppf_server_t s, int n, const int* slots, const void* const* chunks,
+                                    const int64_t* n_samples, void* const* outs, const int64_t* caps, int* statuses);
 
 /* Run one tick on `stream`: every queued chunk of every slot.  *n_done gets the
  * number of chunks processed (may be NULL).  Returns after enqueuing. */

@@ -2,7 +2,7 @@
 // their chunks batched into one set of launches per tick (see include/ppf.h).
 //
 // Per stream the server owns two device buffers (ping-pong) of capacity
-// (T-1)*N + N + max_chunk samples holding the FIR history (Section 2: each
+// 8*T*N + 4*max_chunk + 2*N samples holding the FIR history (Section 2: each
 // output needs the newest sample and T-1 past samples of its channel) plus
 // newly arrived samples.  A tick
 //   1. copies every queued chunk behind its stream's history (one batched
@@ -108,6 +108,11 @@ struct ppf_server_s {
     size_t stage_cap = 0;
     cudaEvent_t stage_free[2] = {nullptr, nullptr};
     int stage_idx = 0;
+    // groups of a tick run concurrently on these streams (fork/join with events)
+    static constexpr int kLanes = 4;
+    cudaStream_t lane[kLanes] = {};
+    cudaEvent_t fork_ev = nullptr;
+    cudaEvent_t join_ev[kLanes] = {};
     int64_t ticks = 0;
     int last_launches = 0;
 };
@@ -149,6 +154,8 @@ void add_copy(std::vector<CopySeg>& segs, const void* src, void* dst, int64_t by
 
 extern "C" {
 
+ppf_status_t ppf_server_destroy(ppf_server_t s);
+
 ppf_status_t ppf_server_create(ppf_server_t* out, int max_streams, size_t memory_budget_bytes)
 {
     if (!out || max_streams < 1 || max_streams > 65536) return PPF_ERR_INVALID_ARG;
@@ -161,8 +168,20 @@ ppf_status_t ppf_server_create(ppf_server_t* out, int max_streams, size_t memory
     cudaError_t e = cudaGetDevice(&dev);
     if (e == cudaSuccess) e = cudaDeviceGetAttribute(&s->sms, cudaDevAttrMultiProcessorCount, dev);
     for (int i = 0; i < 2 && e == cudaSuccess; ++i) e = cudaEventCreateWithFlags(&s->stage_free[i], cudaEventDisableTiming);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&s->fork_ev, cudaEventDisableTiming);
+    for (int i = 0; i < ppf_server_s::kLanes && e == cudaSuccess; ++i) {
+        e = cudaStreamCreateWithFlags(&s->lane[i], cudaStreamNonBlocking);
+        if (e == cudaSuccess) e = cudaEventCreateWithFlags(&s->join_ev[i], cudaEventDisableTiming);
+    }
+    // staging sized up front (64 KiB per stream, 4..64 MiB) so a busy tick
+    // does not stall on a reallocation
+    if (e == cudaSuccess) {
+        const size_t want = std::min<size_t>(64u << 20, std::max<size_t>(4u << 20, (size_t)max_streams << 16));
+        const ppf_status_t ps = grow_stage(s, want);
+        if (ps != PPF_OK) e = cudaErrorMemoryAllocation;
+    }
     if (e != cudaSuccess) {
-        delete s;
+        ppf_server_destroy(s);
         return from_cuda(e);
     }
     *out = s;
@@ -184,9 +203,9 @@ ppf_status_t ppf_server_admit(ppf_server_t s, ppf_plan_t plan, int64_t max_chunk
             break;
         }
     if (free_slot < 0) return PPF_ERR_BUSY;
-    // Two buffers: history ((T-1)*N + N - 1 samples at most) plus several chunks
-    // queued in one tick; rows rounded so every row start is 16-byte aligned.
-    const int64_t cap = ((int64_t)v.T * v.N + 4 * max_chunk_samples + 2 * v.N);
+    // Two buffers, each able to hold four boundary regions (history plus a
+    // prefix, at most 2*T*N samples each) or the history plus four chunks.
+    const int64_t cap = (8 * (int64_t)v.T * v.N + 4 * max_chunk_samples + 2 * v.N);
     const size_t bytes = 2 * (size_t)cap * bps;
     size_t free_b = 0, total_b = 0;
     cudaError_t ce = cudaMemGetInfo(&free_b, &total_b);
@@ -240,7 +259,7 @@ ppf_status_t ppf_server_submit(ppf_server_t s, int slot, const void* d_chunk, in
         return PPF_ERR_INVALID_ARG;
     int64_t queued = 0;
     for (auto& q : sl.queue) queued += q.n;
-    if (sl.held + queued + n_samples > sl.cap) return PPF_ERR_BUSY;  // tick first
+    if (sl.queue.size() >= 4) return PPF_ERR_BUSY;  // at most four chunks between ticks: tick first
     // spectra this submission completes
     const int64_t N = sl.view.N, T = sl.view.T;
     const int64_t before = std::max<int64_t>(0, (sl.pushed + queued) / N - T + 1);
@@ -249,6 +268,19 @@ ppf_status_t ppf_server_submit(ppf_server_t s, int slot, const void* d_chunk, in
     if (after > before && (!d_out || (reinterpret_cast<uintptr_t>(d_out) & 15u))) return PPF_ERR_MISALIGNED;
     sl.queue.push_back({d_chunk, n_samples, d_out, out_capacity_spectra});
     return PPF_OK;
+}
+
+ppf_status_t ppf_server_submit_many(ppf_server_t s, int n, const int* slots, const void* const* chunks,
+                                    const int64_t* n_samples, void* const* outs, const int64_t* caps, int* statuses)
+{
+    if (!s || n < 0 || (n > 0 && (!slots || !chunks || !n_samples || !outs || !caps))) return PPF_ERR_INVALID_ARG;
+    int bad = 0;
+    for (int i = 0; i < n; ++i) {
+        const ppf_status_t st = ppf_server_submit(s, slots[i], chunks[i], n_samples[i], outs[i], caps[i]);
+        if (statuses) statuses[i] = (int)st;
+        bad += st != PPF_OK;
+    }
+    return bad ? PPF_ERR_BUSY : PPF_OK;
 }
 
 ppf_status_t ppf_server_tick(ppf_server_t s, void* stream, int* n_done)
@@ -277,59 +309,117 @@ ppf_status_t ppf_server_tick(ppf_server_t s, void* stream, int* n_done)
     };
     std::vector<Single> singles;
     int processed = 0;
+    bool encode_failed = false;
+    auto add_job = [&](ppf_server_s::Slot& sl, const void* in, float2* out, int64_t count) {
+        const int64_t T = sl.view.T;
+        if (sl.entry.launch_work) {
+            char key[160];
+            std::snprintf(key, sizeof(key), "%d:%d:%d:%s", sl.view.N, sl.view.T, sl.view.dtype, sl.entry.name);
+            auto it = groups.find(key);
+            if (it == groups.end()) {
+                groups[key] = G{sl.view, sl.entry, {}, {}};
+                order.push_back(key);
+                it = groups.find(key);
+            }
+            ppf::PpfJob j{};
+            j.x = in;
+            j.Y = out;
+            j.h = sl.view.h;
+            j.S = count;
+            if (sl.entry.encode) {
+                std::vector<unsigned char> m(128, 0);
+                if (!sl.entry.encode(m.data(), in, count + T - 1)) encode_failed = true;
+                it->second.maps.push_back(std::move(m));
+            }
+            it->second.jobs.push_back(j);
+        } else {
+            singles.push_back({sl.view, sl.entry, in, out, count});
+        }
+    };
     for (auto& sl : s->slots) {
         if (!sl.used || sl.queue.empty()) continue;
-        const int64_t N = sl.view.N, T = sl.view.T;
-        unsigned char* cur = sl.buf[sl.cur];
+        const int64_t N = sl.view.N, T = sl.view.T, B = sl.bps;
+        unsigned char* H = sl.buf[sl.cur];      // persistent history, starts at stream sample base
+        unsigned char* O = sl.buf[sl.cur ^ 1];  // scratch for boundary regions during the tick
         sl.done.assign(sl.queue.size(), 0);
+        // The history (stream samples [emitted*N, pushed)) as (pointer, length).
+        // It starts at H[0]; afterwards it is the tail of a chunk or the tail
+        // of a boundary region.  A region is extended in place when the
+        // history is its tail, and a new region is started in O otherwise, so
+        // every copy of the tick reads only chunks or H and no copy reads
+        // what another copy of the same launch writes.
+        const unsigned char* hist = H;
+        int64_t hist_len = sl.held;
+        unsigned char* tail_end = H + sl.held * B;  // end of the region holding the history
+        int64_t o_off = 0;                          // samples of O used by regions this tick
         for (size_t qi = 0; qi < sl.queue.size(); ++qi) {
             const auto& q = sl.queue[qi];
-            if (q.n > 0) add_copy(gather, q.chunk, cur + sl.held * sl.bps, q.n * sl.bps);
-            sl.held += q.n;
-            sl.pushed += q.n;
-            const int64_t complete = std::max<int64_t>(0, sl.pushed / N - T + 1);
-            const int64_t fresh = complete - sl.emitted;
-            if (fresh > 0) {
-                const void* in = cur + (sl.emitted * N - sl.base) * sl.bps;
-                float2* out = static_cast<float2*>(q.out);
-                if (sl.entry.launch_work) {
-                    char key[160];
-                    std::snprintf(key, sizeof(key), "%d:%d:%d:%s", sl.view.N, sl.view.T, sl.view.dtype, sl.entry.name);
-                    auto it = groups.find(key);
-                    if (it == groups.end()) {
-                        groups[key] = G{sl.view, sl.entry, {}, {}};
-                        order.push_back(key);
-                        it = groups.find(key);
-                    }
-                    ppf::PpfJob j{};
-                    j.x = in;
-                    j.Y = out;
-                    j.h = sl.view.h;
-                    j.S = fresh;
-                    if (sl.entry.encode) {
-                        std::vector<unsigned char> m(128, 0);
-                        if (!sl.entry.encode(m.data(), in, fresh + T - 1)) return PPF_ERR_INVALID_ARG;
-                        it->second.maps.push_back(std::move(m));
-                    }
-                    it->second.jobs.push_back(j);
-                } else {
-                    singles.push_back({sl.view, sl.entry, in, out, fresh});
-                }
-                sl.done[qi] = fresh;
-                sl.emitted = complete;
+            const int64_t P = sl.pushed, n = q.n, total = P + n;
+            if (n == 0) {
+                ++processed;
+                continue;
             }
+            const int64_t e = sl.emitted;
+            const int64_t complete = std::max<int64_t>(e, total / N - T + 1);
+            const unsigned char* chunk = static_cast<const unsigned char*>(q.chunk);
+            const int64_t r0 = (P + N - 1) / N;              // first row starting in the chunk
+            const int64_t s1 = std::max(e, r0);              // spectra read in place: [s1, complete)
+            const int64_t bnd_end = std::min(s1, complete);  // spectra needing the history: [e, bnd_end)
+            const unsigned char* main_in = chunk + (s1 * N - P) * B;
+            const bool in_place = complete > e && complete * N >= P &&
+                                  (complete <= s1 || (reinterpret_cast<uintptr_t>(main_in) & 15u) == 0);
+            // samples of the chunk the boundary region needs: the prefix that
+            // completes spectra [e, bnd_end), or the whole chunk otherwise
+            const int64_t prefix = in_place ? (bnd_end > e ? std::min(total, (bnd_end - 1 + T) * N) - P : 0) : n;
+            const unsigned char* region = nullptr;
+            if (prefix > 0) {
+                if (hist + hist_len * B == tail_end) {
+                    // the history is the tail of the current region: extend it
+                    add_copy(gather, chunk, tail_end, prefix * B);
+                    region = hist;
+                    tail_end += prefix * B;
+                    if (tail_end > O && tail_end <= O + sl.cap * B) o_off = (tail_end - O) / B;
+                } else {
+                    // the history is the tail of a chunk: new region in O (16-byte aligned)
+                    const int64_t align = 16 / B;
+                    o_off = (o_off + align - 1) / align * align;
+                    unsigned char* r = O + o_off * B;
+                    if (hist_len > 0) add_copy(gather, hist, r, hist_len * B);
+                    add_copy(gather, chunk, r + hist_len * B, prefix * B);
+                    o_off += hist_len + prefix;
+                    region = r;
+                    tail_end = r + (hist_len + prefix) * B;
+                }
+            }
+            float2* out = static_cast<float2*>(q.out);
+            if (in_place) {
+                if (bnd_end > e) add_job(sl, region, out, bnd_end - e);
+                if (complete > s1) add_job(sl, main_in, out + (s1 - e) * N, complete - s1);
+                hist = chunk + (complete * N - P) * B;
+            } else {
+                if (complete > e) add_job(sl, region, out, complete - e);
+                hist = region + (complete - e) * N * B;
+            }
+            hist_len = total - complete * N;
+            sl.done[qi] = complete - e;
+            sl.emitted = complete;
+            sl.pushed = total;
             ++processed;
         }
-        // new history: from the first row of the next spectrum to the end
-        const int64_t drop = sl.emitted * N - sl.base;
-        const int64_t keep = sl.held - drop;
-        unsigned char* other = sl.buf[sl.cur ^ 1];
-        if (keep > 0) add_copy(carry, cur + drop * sl.bps, other, keep * sl.bps);
-        sl.cur ^= 1;
-        sl.base += drop;
-        sl.held = keep;
+        // carry the history into a buffer the next tick can extend
+        if (hist == H) {
+            // unchanged start: nothing to move
+        } else if (hist >= H && hist < H + sl.cap * B) {
+            if (hist_len > 0) add_copy(carry, hist, O, hist_len * B);
+            sl.cur ^= 1;
+        } else {
+            if (hist_len > 0) add_copy(carry, hist, H, hist_len * B);
+        }
+        sl.base = sl.emitted * N;
+        sl.held = hist_len;
         sl.queue.clear();
     }
+    if (encode_failed) return PPF_ERR_INVALID_ARG;
     if (processed == 0) return PPF_OK;
 
     // 2. items for each group (about one per resident CTA or cluster)
@@ -355,7 +445,10 @@ ppf_status_t ppf_server_tick(ppf_server_t s, void* stream, int* n_done)
         const int units = std::max(1, g.view.grid_cap / g.entry.cluster);
         int64_t total = 0;
         for (auto& j : g.jobs) total += (j.S + RB - 1) / RB;
-        const int64_t target = std::max<int64_t>(1, (total + units - 1) / units);
+        // pieces of about a quarter of a unit's share, but long enough that
+        // the T-1 halo rows and the pipeline fill stay small against the work
+        const int64_t min_len = std::max<int64_t>(8, (4 * (int64_t)g.view.T + RB - 1) / RB);
+        const int64_t target = std::max<int64_t>(min_len, (total + 4 * units - 1) / (4 * units));
         for (size_t ji = 0; ji < g.jobs.size(); ++ji) {
             const int64_t nblk = (g.jobs[ji].S + RB - 1) / RB;
             const int64_t pieces = std::max<int64_t>(1, (nblk + target / 2) / target);
@@ -367,6 +460,10 @@ ppf_status_t ppf_server_tick(ppf_server_t s, void* stream, int* n_done)
                 if (it.bhi > it.blo) tb.items.push_back(it);
             }
         }
+        // largest first: round-robin over units then balances like LPT
+        std::stable_sort(tb.items.begin(), tb.items.end(), [](const ppf::PpfItem& a, const ppf::PpfItem& b) {
+            return (a.bhi - a.blo) > (b.bhi - b.blo);
+        });
         tb.grid = std::min<int>(units, (int)tb.items.size()) * g.entry.cluster;
         tb.maps_at = place(128 * g.maps.size(), 128);
         tb.jobs_at = place(sizeof(ppf::PpfJob) * g.jobs.size(), 16);
@@ -410,15 +507,26 @@ ppf_status_t ppf_server_tick(ppf_server_t s, void* stream, int* n_done)
         ppf::note_launch();
         ++launches;
     }
-    for (size_t gi = 0; gi < order.size() && e == cudaSuccess; ++gi) {
+    // PPF groups run concurrently on the lanes, forked from and joined back
+    // into the caller's stream, so one group's tail overlaps the next's start
+    const int nwork = (int)order.size() + (int)singles.size();
+    const int nl = std::min(ppf_server_s::kLanes, std::max(1, nwork));
+    if (e == cudaSuccess) e = cudaEventRecord(s->fork_ev, st);
+    for (int l = 0; l < nl && e == cudaSuccess; ++l) e = cudaStreamWaitEvent(s->lane[l], s->fork_ev, 0);
+    int w = 0;
+    for (size_t gi = 0; gi < order.size() && e == cudaSuccess; ++gi, ++w) {
         G& g = groups[order[gi]];
-        e = g.entry.launch_work(g.view, works[gi], tabs[gi].grid, st);
+        e = g.entry.launch_work(g.view, works[gi], tabs[gi].grid, s->lane[w % nl]);
         ++launches;
     }
     for (auto& sg : singles) {
         if (e != cudaSuccess) break;
-        e = sg.entry.launch(sg.view, sg.in, sg.out, sg.S, st);
+        e = sg.entry.launch(sg.view, sg.in, sg.out, sg.S, s->lane[w++ % nl]);
         ++launches;
+    }
+    for (int l = 0; l < nl && e == cudaSuccess; ++l) {
+        e = cudaEventRecord(s->join_ev[l], s->lane[l]);
+        if (e == cudaSuccess) e = cudaStreamWaitEvent(st, s->join_ev[l], 0);
     }
     if (e == cudaSuccess && !carry.empty()) {
         const int kgrid = std::max(1, std::min<int>((int)carry.size(), 4 * s->sms));
@@ -465,6 +573,11 @@ ppf_status_t ppf_server_destroy(ppf_server_t s)
         if (s->dev_stage[i]) cudaFree(s->dev_stage[i]);
         if (s->stage_free[i]) cudaEventDestroy(s->stage_free[i]);
     }
+    for (int i = 0; i < ppf_server_s::kLanes; ++i) {
+        if (s->lane[i]) cudaStreamDestroy(s->lane[i]);
+        if (s->join_ev[i]) cudaEventDestroy(s->join_ev[i]);
+    }
+    if (s->fork_ev) cudaEventDestroy(s->fork_ev);
     delete s;
     return from_cuda(e);
 }

@@ -32,7 +32,7 @@ EXPORTS = ("ppf_plan_create", "ppf_plan_destroy", "ppf_execute", "ppf_execute_ho
            "ppf_status_string", "ppf_plan_kernel_name", "ppf_launch_count", "ppf_variant_count",
            "ppf_variant_name", "ppf_execute_noalloc", "ppf_batch_create", "ppf_batch_execute",
            "ppf_batch_launches", "ppf_batch_destroy", "ppf_server_create", "ppf_server_admit",
-           "ppf_server_release", "ppf_server_submit", "ppf_server_tick", "ppf_server_position",
+           "ppf_server_release", "ppf_server_submit", "ppf_server_submit_many", "ppf_server_tick", "ppf_server_position",
            "ppf_server_info", "ppf_server_destroy")
 
 
@@ -90,6 +90,7 @@ def load(path: str | None = None):
             "ppf_server_admit": ([vp, vp, i64, ctypes.POINTER(i32)], i32),
             "ppf_server_release": ([vp, i32], i32),
             "ppf_server_submit": ([vp, i32, vp, i64, vp, i64], i32),
+            "ppf_server_submit_many": ([vp, i32, vp, vp, vp, vp, vp, vp], i32),
             "ppf_server_tick": ([vp, vp, ctypes.POINTER(i32)], i32),
             "ppf_server_position": ([vp, i32, ctypes.POINTER(i64), ctypes.POINTER(i64)], i32),
             "ppf_server_info": ([vp, ctypes.POINTER(ctypes.c_size_t), ctypes.POINTER(i32), ctypes.POINTER(i32)], i32),
@@ -389,6 +390,23 @@ class Server:
         cap = out.numel() // self.plans[slot].N if out is not None else 0
         st = load().ppf_server_submit(self.handle, int(slot), chunk.data_ptr() if n else None, n,
                                       out.data_ptr() if (out is not None and out.numel()) else None, cap)
+        return st
+
+    def submit_many(self, slots, chunk_ptrs, n_samples, out_ptrs, caps):
+        """Queue many chunks in one call; numpy arrays (int32 slots, int64 pointers/sizes).
+
+        Returns the per-chunk status array.
+        """
+        import numpy as np
+        slots = np.ascontiguousarray(slots, dtype=np.int32)
+        chunk_ptrs = np.ascontiguousarray(chunk_ptrs, dtype=np.uint64)
+        n_samples = np.ascontiguousarray(n_samples, dtype=np.int64)
+        out_ptrs = np.ascontiguousarray(out_ptrs, dtype=np.uint64)
+        caps = np.ascontiguousarray(caps, dtype=np.int64)
+        st = np.zeros(slots.shape[0], dtype=np.int32)
+        load().ppf_server_submit_many(self.handle, int(slots.shape[0]), slots.ctypes.data, chunk_ptrs.ctypes.data,
+                                      n_samples.ctypes.data, out_ptrs.ctypes.data, caps.ctypes.data,
+                                      st.ctypes.data)
         return st
 
     def tick(self, stream=None) -> int:
