@@ -34,7 +34,10 @@
  *     waiting.  Argument errors are reported synchronously and enqueue
  *     nothing.  Errors of earlier asynchronous work surface as PPF_ERR_CUDA.
  *   - A plan is immutable after creation and may be used from several host
- *     threads and streams at once.  A stream object is not thread-safe.
+ *     threads at once.  Executions of one plan on different CUDA streams must
+ *     be ordered when its kernel uses plan-owned scratch (the cooperative
+ *     split kernel for large N*T, see ppf_plan_kernel_name "split:..."); use
+ *     one plan per stream otherwise.  A stream object is not thread-safe.
  */
 #ifndef PPF_H_
 #define PPF_H_

@@ -39,6 +39,7 @@ struct ppf_plan_s {
     void* d_h = nullptr;
     float2* d_tw = nullptr;
     int* h_err = nullptr;    // mapped host word a kernel sets when a bounded wait gives up
+    void* d_scratch = nullptr;  // kernel scratch (split kernel: group counters and exchange rows)
     // staging for ppf_execute_host (allocated on first use)
     std::mutex host_mu;
     void* d_stage_in[2] = {nullptr, nullptr};
@@ -112,6 +113,7 @@ void free_plan_memory(ppf_plan_s* p)
     if (p->d_h) cudaFree(p->d_h);
     if (p->d_tw) cudaFree(p->d_tw);
     if (p->h_err) cudaFreeHost(p->h_err);
+    if (p->d_scratch) cudaFree(p->d_scratch);
     for (int i = 0; i < 2; ++i) {
         if (p->d_stage_in[i]) cudaFree(p->d_stage_in[i]);
         if (p->d_stage_out[i]) cudaFree(p->d_stage_out[i]);
@@ -227,6 +229,11 @@ ppf_status_t ppf_plan_create(ppf_plan_t* out, int N, int T, const float* h_host,
     }
     e = p->entry.prepare(p->view);
     if (e == cudaSuccess) e = p->fir_entry.prepare(p->fir_view);
+    if (e == cudaSuccess && p->view.scratch_bytes > 0) {
+        e = cudaMalloc(&p->d_scratch, p->view.scratch_bytes);
+        if (e == cudaSuccess) e = cudaMemset(p->d_scratch, 0, p->view.scratch_bytes);
+        p->view.scratch = p->d_scratch;
+    }
     if (e != cudaSuccess) {
         free_plan_memory(p);
         delete p;

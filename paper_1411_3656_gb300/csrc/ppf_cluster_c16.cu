@@ -8,6 +8,10 @@ static int variants_impl(int N, int T, int want, KernelEntry* out)
 {
     int idx = 0;
 #include "ppf_cluster_table.inc"
+    // N1 = 32: longer output runs (K2 = N2/P consecutive bins), 32-byte input rows
+    PPF_CV(4096, 4, 8, 32, 256, 4, 3, 1) PPF_CV(4096, 8, 8, 32, 256, 4, 4, 1)
+    PPF_CV(4096, 16, 8, 32, 256, 4, 6, 1) PPF_CV(4096, 32, 8, 32, 256, 4, 10, 1)
+    PPF_CV(2048, 8, 4, 32, 256, 4, 4, 1) PPF_CV(2048, 16, 4, 32, 256, 4, 6, 1)
     return idx;
 }
 

@@ -17,6 +17,8 @@ struct PlanView {
     int grid_cap = 0;             // resident CTAs for the chosen kernel (set by prepare)
     int fir_only = 0;             // test hook: store y instead of Y
     int* err = nullptr;           // device-visible error word (mapped host memory)
+    void* scratch = nullptr;      // plan-owned device scratch (split kernel: counters + exchange rows)
+    size_t scratch_bytes = 0;     // set by prepare; the plan allocates it
 };
 
 using PrepareFn = cudaError_t (*)(PlanView&);

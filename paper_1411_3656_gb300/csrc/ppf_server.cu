@@ -519,9 +519,11 @@ ppf_status_t ppf_server_tick(ppf_server_t s, void* stream, int* n_done)
         e = g.entry.launch_work(g.view, works[gi], tabs[gi].grid, s->lane[w % nl]);
         ++launches;
     }
+    // jobs on kernels without a work-list form may use their plan's scratch:
+    // one lane runs them one after another
     for (auto& sg : singles) {
         if (e != cudaSuccess) break;
-        e = sg.entry.launch(sg.view, sg.in, sg.out, sg.S, s->lane[w++ % nl]);
+        e = sg.entry.launch(sg.view, sg.in, sg.out, sg.S, s->lane[0]);
         ++launches;
     }
     for (int l = 0; l < nl && e == cudaSuccess; ++l) {
