@@ -54,6 +54,8 @@ def parse():
     ap.add_argument("--dtype", choices=("c32", "c16", "ci8"), default="c32")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-unfused", action="store_true",
+                    help="skip the unfused comparison (FIR-only kernel to HBM, then cuFFT), timed once per cell")
     ap.add_argument("--cpu-seconds", type=float, default=15.0, help="CPU budget of the oracle baseline")
     ap.add_argument("--cells-out", default="", help="also write the per-cell table as JSON here")
     ap.add_argument("--variant", type=int, default=-1, help="force kernel variant i (profiling one cell)")
@@ -255,6 +257,52 @@ def run_reference(args):
 
 
 # ----------------------------------------------------------------- our arm
+def unfused_comparison(args, plans, x_dev, y_dev, cell_rows, stream, dev):
+    """The paper's two-pass design on the same GPU: a FIR-only kernel writes the
+    filtered spectra to HBM and cuFFT (torch.fft) transforms them.  Timed once per
+    cell (median of 3, CUDA events), outside the timed steps; adds `unfused_ms`
+    to each cell row.  The FIR pass is this library's general kernel in its
+    FIR-only mode, not tuned for the role."""
+    import torch
+
+    from paper_1411_3656_gb300 import ppf, synth
+
+    try:
+        y_fir = torch.empty_like(y_dev)
+        sp = stream.cuda_stream
+        tot_fused = tot_unfused = 0.0
+        for row, (N, T, S, plan) in zip(cell_rows, plans):
+            fir = ppf.Plan(N, T, synth.hamming_sinc(N, T), args.dtype, ppf.FLAG_FIR_ONLY)
+            yv = y_fir[:S * N].view(S, N)
+            Yv = y_dev[:S * N].view(S, N)
+            times = []
+            for _ in range(4):
+                e0, e1, e2 = (torch.cuda.Event(enable_timing=True) for _ in range(3))
+                e0.record(stream)
+                st = ppf.ppf_execute(fir.handle, x_dev.data_ptr(), y_fir.data_ptr(), S, sp)
+                if st != 0:
+                    raise ppf.PPFError(st, "ppf_execute (FIR only)")
+                e1.record(stream)
+                torch.fft.fft(yv, dim=-1, out=Yv)
+                e2.record(stream)
+                torch.cuda.synchronize(dev)
+                times.append((e0.elapsed_time(e1), e1.elapsed_time(e2)))
+            times = sorted(times[1:], key=lambda t: t[0] + t[1])[1]
+            row["unfused_ms"] = round(times[0] + times[1], 4)
+            row["unfused_fir_ms"] = round(times[0], 4)
+            row["unfused_fft_ms"] = round(times[1], 4)
+            tot_fused += row["ms"]
+            tot_unfused += times[0] + times[1]
+            fir.close()
+        del y_fir
+        torch.cuda.empty_cache()
+        return {"ms_per_step": tot_unfused, "fused_ms_per_step": tot_fused,
+                "fused_speedup": tot_unfused / tot_fused,
+                "design": "FIR-only kernel (general, FIR-only mode) -> HBM -> cuFFT C2C via torch.fft"}
+    except Exception as e:  # a comparison only: report, do not fail the bench
+        return {"error": f"{type(e).__name__}: {e}"[:200]}
+
+
 def run_ours(args):
     import numpy as np
     import torch
@@ -377,6 +425,10 @@ def run_ours(args):
                "steps": e_steps, "x_realtime": data_s * e_steps / e_el, "api": "ppf_execute_host"}
         del xh, yh
 
+    unfused = None
+    if rank == 0 and world == 1 and not args.no_unfused and args.workload == "realtime_sweep":
+        unfused = unfused_comparison(args, plans, x_dev, y_dev, cell_rows, stream, dev)
+
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         v, cores, desc = oracle_baseline(args, cells, x_host, args.cpu_seconds)
@@ -406,6 +458,7 @@ def run_ours(args):
             "e2e": e2e,
             "gpu_launches": launches,
             "cpu_baseline": cpu,
+            "unfused": unfused,
             "cells": cell_rows,
         }
         print(json.dumps(line), flush=True)

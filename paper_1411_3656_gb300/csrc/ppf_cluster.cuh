@@ -47,9 +47,13 @@ __host__ __device__ constexpr int stage2_stride(int N1, int K2)
     return s;
 }
 
-template <int N_, int T_, class In_, int P_, int N1_, int NT_, int RB_, int NCH_, int MINB_ = 1>
+template <int N_, int T_, class In_, int P_, int N1_, int NT_, int RB_, int NCH_, int MINB_ = 1, int CPT_ = 2>
 struct ClusterCfg {
     static constexpr int N = N_, T = T_, P = P_, N1 = N1_, NT = NT_, RB = RB_, NCH = NCH_, MINB = MINB_;
+    // FIR channels per thread: 2 (a pair, one 2-sample load per row, scalar
+    // FMAs) or 1 (one channel, coefficients duplicated as (h, h) so that one
+    // packed f32x2 FMA updates a complex accumulator)
+    static constexpr int CPT = CPT_;
     using In = In_;
     using raw = typename In::raw;
     using coef_t = typename Coef<In>::type;
@@ -58,9 +62,9 @@ struct ClusterCfg {
     static constexpr int C1 = N1 / P;  // input channels c1 per CTA
     static constexpr int K2 = N2 / P;  // bin groups k2 per CTA
     static constexpr int NC = N / P;   // channels per CTA
-    static constexpr int PAIRS = NC / 2;
-    static constexpr int G = PAIRS > NT ? PAIRS / NT : 1;
-    static constexpr int RG = PAIRS >= NT ? 1 : NT / PAIRS;
+    static constexpr int UNITS = NC / CPT;  // FIR work units per row
+    static constexpr int G = UNITS > NT ? UNITS / NT : 1;
+    static constexpr int RG = UNITS >= NT ? 1 : NT / UNITS;
     static constexpr int RBT = RB / RG;
     static constexpr int KO = T >= 2 ? (T - 2) / RB + 1 : 0;
     static constexpr int RING_ROWS = NCH * RB;
@@ -73,6 +77,8 @@ struct ClusterCfg {
     static constexpr int XBYTES = RB * K2 * N1 * 8;  // bytes each CTA receives per block
     static constexpr int SMEM = RING_BYTES + (A_SLOTS + 2 * X_SLOTS) * 8 + (NCH + 4) * 8;
     static_assert(P >= 2 && P <= 8, "portable cluster sizes");
+    static_assert(CPT == 1 || CPT == 2, "one channel or a pair per thread");
+    static_assert(UNITS % NT == 0 || NT % UNITS == 0, "FIR units must tile the threads");
     static_assert(C1 >= 2 && C1 % 2 == 0 && (C1 * BPS) % 16 == 0, "TMA box rows must be 16-byte multiples");
     static_assert(K2 >= 1 && N2 <= 256 && C1 <= 256 && RB <= 256, "TMA box limits");
     static_assert(RB % RG == 0 && RBT >= 1, "rows per block must split over row groups");
@@ -278,6 +284,7 @@ ppf_cluster_kernel(const __grid_constant__ CUtensorMap xmap, const PpfWork wl, c
     constexpr int N = C::N, T = C::T, NT = C::NT, RB = C::RB, NCH = C::NCH, P = C::P;
     constexpr int G = C::G, RBT = C::RBT, BPS = C::BPS, RING_ROWS = C::RING_ROWS, NC = C::NC, C1 = C::C1;
     using PV = typename Pair<typename C::In>::vec;
+    using raw = typename C::raw;
     using coef_t = typename C::coef_t;
 
     extern __shared__ __align__(128) unsigned char smem[];
@@ -306,9 +313,10 @@ ppf_cluster_kernel(const __grid_constant__ CUtensorMap xmap, const PpfWork wl, c
     cluster_wait_acquire();
     const uint64_t policy = l2_evict_first_policy();
 
-    // FIR ownership: channel pairs (c1l, c1l+1) at c2 of this CTA's slice
-    const int rg = C::PAIRS >= NT ? 0 : tid / C::PAIRS;
-    const int pbase = C::PAIRS >= NT ? tid : tid % C::PAIRS;
+    // FIR ownership: unit pp is channel pair (c1l, c1l+1) at c2 of this CTA's
+    // slice (CPT = 2) or the single channel at ring offset pp (CPT = 1)
+    const int rg = C::UNITS >= NT ? 0 : tid / C::UNITS;
+    const int pbase = C::UNITS >= NT ? tid : tid % C::UNITS;
     const int i0 = rg * RBT;
     StageTwiddles<C::N2, C1, NT> tw1;
     tw1.load(tw, N);
@@ -364,16 +372,28 @@ ppf_cluster_kernel(const __grid_constant__ CUtensorMap xmap, const PpfWork wl, c
             issued = first;
         }
 
-        float hr[G][T][2];
+        // coefficients of the owned channels, in registers for the whole item
+        // (CPT = 1 keeps each as the pair (h, h))
+        float hr[C::CPT == 2 ? G : 1][C::CPT == 2 ? T : 1][2];
+        float2 hh[C::CPT == 1 ? G : 1][C::CPT == 1 ? T : 1];
 #pragma unroll
         for (int g = 0; g < G; ++g) {
             const int pp = pbase + g * NT;
-            const int c1l = 2 * (pp % (C1 / 2)), c2 = pp / (C1 / 2);
-            const int c = rank * C1 + c1l + C::N1 * c2;
+            if constexpr (C::CPT == 2) {
+                const int c1l = 2 * (pp % (C1 / 2)), c2 = pp / (C1 / 2);
+                const int c = rank * C1 + c1l + C::N1 * c2;
 #pragma unroll
-            for (int t = 0; t < T; ++t) {
-                hr[g][t][0] = coef_f(h[t * N + c]);
-                hr[g][t][1] = coef_f(h[t * N + c + 1]);
+                for (int t = 0; t < T; ++t) {
+                    hr[g][t][0] = coef_f(h[t * N + c]);
+                    hr[g][t][1] = coef_f(h[t * N + c + 1]);
+                }
+            } else {
+                const int c = rank * C1 + pp % C1 + C::N1 * (pp / C1);
+#pragma unroll
+                for (int t = 0; t < T; ++t) {
+                    const float v = coef_f(h[t * N + c]);
+                    hh[g][t] = make_float2(v, v);
+                }
             }
         }
 
@@ -401,35 +421,55 @@ ppf_cluster_kernel(const __grid_constant__ CUtensorMap xmap, const PpfWork wl, c
 #pragma unroll
                 for (int g = 0; g < G; ++g) {
                     const int pp = pbase + g * NT;
-                    const int l = (pp / (C1 / 2)) * C1 + 2 * (pp % (C1 / 2));
-                    float2 a0[RBT], a1[RBT];
-#pragma unroll
-                    for (int i = 0; i < RBT; ++i) {
-                        a0[i] = make_float2(0.f, 0.f);
-                        a1[i] = make_float2(0.f, 0.f);
-                    }
-#pragma unroll
-                    for (int u = 0; u < RBT + T - 1; ++u) {
-                        int rr = rrb + i0 + u;
-                        rr = rr >= RING_ROWS ? rr - RING_ROWS : rr;
-                        const PV pv = *reinterpret_cast<const PV*>(ring + ((size_t)rr * NC + l) * BPS);
-                        float2 v0, v1;
-                        Pair<typename C::In>::split(pv, v0, v1);
+                    if constexpr (C::CPT == 2) {
+                        const int l = (pp / (C1 / 2)) * C1 + 2 * (pp % (C1 / 2));
+                        float2 a0[RBT], a1[RBT];
 #pragma unroll
                         for (int i = 0; i < RBT; ++i) {
-                            const int t = u - i;
-                            if (t >= 0 && t < T) {
-                                a0[i].x = fmaf(hr[g][t][0], v0.x, a0[i].x);
-                                a0[i].y = fmaf(hr[g][t][0], v0.y, a0[i].y);
-                                a1[i].x = fmaf(hr[g][t][1], v1.x, a1[i].x);
-                                a1[i].y = fmaf(hr[g][t][1], v1.y, a1[i].y);
+                            a0[i] = make_float2(0.f, 0.f);
+                            a1[i] = make_float2(0.f, 0.f);
+                        }
+#pragma unroll
+                        for (int u = 0; u < RBT + T - 1; ++u) {
+                            int rr = rrb + i0 + u;
+                            rr = rr >= RING_ROWS ? rr - RING_ROWS : rr;
+                            const PV pv = *reinterpret_cast<const PV*>(ring + ((size_t)rr * NC + l) * BPS);
+                            float2 v0, v1;
+                            Pair<typename C::In>::split(pv, v0, v1);
+#pragma unroll
+                            for (int i = 0; i < RBT; ++i) {
+                                const int t = u - i;
+                                if (t >= 0 && t < T) {
+                                    a0[i].x = fmaf(hr[g][t][0], v0.x, a0[i].x);
+                                    a0[i].y = fmaf(hr[g][t][0], v0.y, a0[i].y);
+                                    a1[i].x = fmaf(hr[g][t][1], v1.x, a1[i].x);
+                                    a1[i].y = fmaf(hr[g][t][1], v1.y, a1[i].y);
+                                }
                             }
                         }
-                    }
 #pragma unroll
-                    for (int i = 0; i < RBT; ++i)
-                        *reinterpret_cast<float4*>(A + (i0 + i) * C::RSB + l) =
-                            make_float4(a0[i].x, a0[i].y, a1[i].x, a1[i].y);
+                        for (int i = 0; i < RBT; ++i)
+                            *reinterpret_cast<float4*>(A + (i0 + i) * C::RSB + l) =
+                                make_float4(a0[i].x, a0[i].y, a1[i].x, a1[i].y);
+                    } else {
+                        const int l = pp;
+                        float2 a[RBT];
+#pragma unroll
+                        for (int i = 0; i < RBT; ++i) a[i] = make_float2(0.f, 0.f);
+#pragma unroll
+                        for (int u = 0; u < RBT + T - 1; ++u) {
+                            int rr = rrb + i0 + u;
+                            rr = rr >= RING_ROWS ? rr - RING_ROWS : rr;
+                            const float2 v = decode(*reinterpret_cast<const raw*>(ring + ((size_t)rr * NC + l) * BPS));
+#pragma unroll
+                            for (int i = 0; i < RBT; ++i) {
+                                const int t = u - i;
+                                if (t >= 0 && t < T) a[i] = __ffma2_rn(hh[g][t], v, a[i]);
+                            }
+                        }
+#pragma unroll
+                        for (int i = 0; i < RBT; ++i) A[(i0 + i) * C::RSB + l] = a[i];
+                    }
                 }
                 __syncthreads();
                 if (tid == 0 && !failed && issued < nchunks && issued == b + NCH) {

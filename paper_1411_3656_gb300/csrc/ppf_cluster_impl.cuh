@@ -128,8 +128,8 @@ template <class C>
 KernelEntry entry()
 {
     static char name[80];
-    std::snprintf(name, sizeof(name), "cluster:p%d:n1_%d:nt%d:rb%d:nch%d:b%d", C::P, C::N1, C::NT, C::RB, C::NCH,
-                  C::MINB);
+    std::snprintf(name, sizeof(name), "cluster:p%d:n1_%d:nt%d:rb%d:nch%d:b%d%s", C::P, C::N1, C::NT, C::RB, C::NCH,
+                  C::MINB, C::CPT == 1 ? ":c1" : "");
     KernelEntry e;
     e.name = name;
     e.prepare = prepare_cluster<C>;
@@ -144,10 +144,17 @@ KernelEntry entry()
 }  // namespace cluster_detail
 }  // namespace ppf
 
-// PPF_CV(N, T, P, N1, NT, RB, NCH, MINB): one cluster-kernel variant.
+// PPF_CV(N, T, P, N1, NT, RB, NCH, MINB): one cluster-kernel variant (a
+// channel pair per FIR thread); PPF_CV1: the same with one channel per thread.
 #define PPF_CV(NN, TT, P, N1, NT, RB, NCH, MINB)                                                        \
     if (N == NN && T == TT) {                                                                           \
         if (idx == want && out)                                                                         \
             *out = cluster_detail::entry<ClusterCfg<NN, TT, In, P, N1, NT, RB, NCH, MINB>>();           \
+        ++idx;                                                                                          \
+    }
+#define PPF_CV1(NN, TT, P, N1, NT, RB, NCH, MINB)                                                       \
+    if (N == NN && T == TT) {                                                                           \
+        if (idx == want && out)                                                                         \
+            *out = cluster_detail::entry<ClusterCfg<NN, TT, In, P, N1, NT, RB, NCH, MINB, 1>>();        \
         ++idx;                                                                                          \
     }

@@ -7,10 +7,10 @@
 // T-1 rows a block shares with the next stay in the ring.  Per block:
 //
 //   1. wait for the chunk holding the block's newest rows (bounded wait);
-//   2. FIR (Section 2, Eq. 1): each thread owns channel pairs (2p, 2p+1), keeps
-//      their 2T coefficients in registers and produces RBT consecutive spectra
-//      from RBT+T-1 ring rows (register blocking: each shared-memory read feeds
-//      up to RBT multiply-adds per channel);
+//   2. FIR (Section 2, Eq. 1): each thread owns channel pairs (2p, 2p+1), or
+//      single channels, keeps their coefficients in registers and produces RBT
+//      consecutive spectra from RBT+T-1 ring rows (register blocking: each
+//      shared-memory read feeds up to RBT multiply-adds per channel);
 //   3. refill the ring slot the block no longer needs;
 //   4. FFT of the RB filtered rows with Stockham radix-16 passes ping-ponging
 //      between two shared buffers; the last pass stores the spectra to global
@@ -23,17 +23,21 @@
 
 namespace ppf {
 
-template <int N_, int T_, class In_, int NT_, int RB_, int NCH_, int MINB_ = 1>
+template <int N_, int T_, class In_, int NT_, int RB_, int NCH_, int MINB_ = 1, int CPT_ = 2>
 struct RingCfg {
     static constexpr int N = N_, T = T_, NT = NT_, RB = RB_, NCH = NCH_, MINB = MINB_;
+    // FIR channels per thread: 2 (a pair, one 2-sample load per row, scalar
+    // FMAs) or 1 (one channel, coefficients duplicated as (h, h) so that one
+    // packed f32x2 FMA updates a complex accumulator)
+    static constexpr int CPT = CPT_;
     using In = In_;
     using raw = typename In::raw;
     using coef_t = typename Coef<In>::type;
     static constexpr int BPS = In::bytes;
     static constexpr int RS = fft_row_stride(N);
-    static constexpr int PAIRS = N / 2;
-    static constexpr int G = PAIRS > NT ? PAIRS / NT : 1;     // channel pairs per thread
-    static constexpr int RG = PAIRS >= NT ? 1 : NT / PAIRS;   // row groups
+    static constexpr int UNITS = N / CPT;                     // FIR work units per row
+    static constexpr int G = UNITS > NT ? UNITS / NT : 1;     // units per thread
+    static constexpr int RG = UNITS >= NT ? 1 : NT / UNITS;   // row groups
     static constexpr int RBT = RB / RG;                       // spectra per thread per block
     static constexpr int KO = T >= 2 ? (T - 2) / RB + 1 : 0;  // chunks beyond the block's first
     static constexpr int RING_ROWS = NCH * RB;
@@ -43,6 +47,8 @@ struct RingCfg {
     static constexpr int FFT_BYTES = 2 * BUF_SLOTS * 8;
     static constexpr int SMEM = RING_BYTES + FFT_BYTES + NCH * 8;
     static_assert(N >= 64, "ring kernel handles N >= 64");
+    static_assert(CPT == 1 || CPT == 2, "one channel or a pair per thread");
+    static_assert(UNITS % NT == 0 || NT % UNITS == 0, "FIR units must tile the threads");
     static_assert(RB % RG == 0 && RBT >= 1, "rows per block must split over row groups");
     static_assert(NCH >= KO + 2, "ring must hold a block's window plus one chunk in flight");
     static_assert(CHUNK_BYTES % 16 == 0, "bulk copies move multiples of 16 bytes");
@@ -118,9 +124,9 @@ ppf_ring_kernel(const PpfWork wl, const float2* __restrict__ tw, int* __restrict
     __syncthreads();
     const uint64_t policy = l2_evict_first_policy();
 
-    // Thread -> (row group, channel pairs).
-    const int rg = C::PAIRS >= NT ? 0 : tid / C::PAIRS;
-    const int pbase = C::PAIRS >= NT ? tid : tid % C::PAIRS;
+    // Thread -> (row group, FIR units: channel pairs or single channels).
+    const int rg = C::UNITS >= NT ? 0 : tid / C::UNITS;
+    const int pbase = C::UNITS >= NT ? tid : tid % C::UNITS;
     const int i0 = rg * RBT;
     PassTwiddles<N, NT> twr;
     twr.load(tw);
@@ -170,15 +176,22 @@ ppf_ring_kernel(const PpfWork wl, const float2* __restrict__ tw, int* __restrict
             issued = first;
         }
 
-        // coefficients of this thread's channels, in FP32 registers
-        float hr[G][T][2];
+        // coefficients of this thread's channels, in FP32 registers (CPT = 1
+        // keeps each as the pair (h, h))
+        float hr[C::CPT == 2 ? G : 1][C::CPT == 2 ? T : 1][2];
+        float2 hh[C::CPT == 1 ? G : 1][C::CPT == 1 ? T : 1];
 #pragma unroll
         for (int g = 0; g < G; ++g) {
-            const int c = 2 * (pbase + g * NT);
+            const int c = C::CPT * (pbase + g * NT);
 #pragma unroll
             for (int t = 0; t < T; ++t) {
-                hr[g][t][0] = coef_f(h[t * N + c]);
-                hr[g][t][1] = coef_f(h[t * N + c + 1]);
+                if constexpr (C::CPT == 2) {
+                    hr[g][t][0] = coef_f(h[t * N + c]);
+                    hr[g][t][1] = coef_f(h[t * N + c + 1]);
+                } else {
+                    const float v = coef_f(h[t * N + c]);
+                    hh[g][t] = make_float2(v, v);
+                }
             }
         }
 
@@ -201,38 +214,57 @@ ppf_ring_kernel(const PpfWork wl, const float2* __restrict__ tw, int* __restrict
                 break;
             }
 
-            // 2. FIR over the ring (Eq. 1), RBT spectra x 2 channels per pair
+            // 2. FIR over the ring (Eq. 1), RBT spectra x CPT channels per unit
 #pragma unroll
             for (int g = 0; g < G; ++g) {
-                const int c = 2 * (pbase + g * NT);
-                float2 a0[RBT], a1[RBT];
-#pragma unroll
-                for (int i = 0; i < RBT; ++i) {
-                    a0[i] = make_float2(0.f, 0.f);
-                    a1[i] = make_float2(0.f, 0.f);
-                }
-#pragma unroll
-                for (int u = 0; u < RBT + T - 1; ++u) {
-                    int rr = rrb + i0 + u;
-                    rr = rr >= RING_ROWS ? rr - RING_ROWS : rr;
-                    const PV pv = *reinterpret_cast<const PV*>(ring + ((size_t)rr * N + c) * BPS);
-                    float2 v0, v1;
-                    Pair<typename C::In>::split(pv, v0, v1);
+                const int c = C::CPT * (pbase + g * NT);
+                if constexpr (C::CPT == 2) {
+                    float2 a0[RBT], a1[RBT];
 #pragma unroll
                     for (int i = 0; i < RBT; ++i) {
-                        const int t = u - i;
-                        if (t >= 0 && t < T) {
-                            a0[i].x = fmaf(hr[g][t][0], v0.x, a0[i].x);
-                            a0[i].y = fmaf(hr[g][t][0], v0.y, a0[i].y);
-                            a1[i].x = fmaf(hr[g][t][1], v1.x, a1[i].x);
-                            a1[i].y = fmaf(hr[g][t][1], v1.y, a1[i].y);
+                        a0[i] = make_float2(0.f, 0.f);
+                        a1[i] = make_float2(0.f, 0.f);
+                    }
+#pragma unroll
+                    for (int u = 0; u < RBT + T - 1; ++u) {
+                        int rr = rrb + i0 + u;
+                        rr = rr >= RING_ROWS ? rr - RING_ROWS : rr;
+                        const PV pv = *reinterpret_cast<const PV*>(ring + ((size_t)rr * N + c) * BPS);
+                        float2 v0, v1;
+                        Pair<typename C::In>::split(pv, v0, v1);
+#pragma unroll
+                        for (int i = 0; i < RBT; ++i) {
+                            const int t = u - i;
+                            if (t >= 0 && t < T) {
+                                a0[i].x = fmaf(hr[g][t][0], v0.x, a0[i].x);
+                                a0[i].y = fmaf(hr[g][t][0], v0.y, a0[i].y);
+                                a1[i].x = fmaf(hr[g][t][1], v1.x, a1[i].x);
+                                a1[i].y = fmaf(hr[g][t][1], v1.y, a1[i].y);
+                            }
                         }
                     }
-                }
 #pragma unroll
-                for (int i = 0; i < RBT; ++i)
-                    *reinterpret_cast<float4*>(bufA + (i0 + i) * RS + c) =
-                        make_float4(a0[i].x, a0[i].y, a1[i].x, a1[i].y);
+                    for (int i = 0; i < RBT; ++i)
+                        *reinterpret_cast<float4*>(bufA + (i0 + i) * RS + c) =
+                            make_float4(a0[i].x, a0[i].y, a1[i].x, a1[i].y);
+                } else {
+                    float2 a[RBT];
+#pragma unroll
+                    for (int i = 0; i < RBT; ++i) a[i] = make_float2(0.f, 0.f);
+#pragma unroll
+                    for (int u = 0; u < RBT + T - 1; ++u) {
+                        int rr = rrb + i0 + u;
+                        rr = rr >= RING_ROWS ? rr - RING_ROWS : rr;
+                        const float2 v = decode(*reinterpret_cast<const raw*>(ring + ((size_t)rr * N + c) * BPS));
+#pragma unroll
+                        for (int i = 0; i < RBT; ++i) {
+                            const int t = u - i;
+                            if (t >= 0 && t < T) a[i] = __ffma2_rn(hh[g][t], v, a[i]);
+                        }
+                    }
+#pragma unroll
+                    for (int i = 0; i < RBT; ++i) bufA[(i0 + i) * RS + c] = a[i];
+                }
             }
             __syncthreads();
 

@@ -8,6 +8,13 @@ static int variants_impl(int N, int T, int want, KernelEntry* out)
 {
     int idx = 0;
 #include "ppf_ring_table.inc"
+    // one channel per FIR thread, packed f32x2 FMAs
+    PPF_RV1(256, 8, 256, 16, 4, 1) PPF_RV1(256, 16, 256, 16, 4, 1)
+    PPF_RV1(256, 32, 256, 16, 4, 1) PPF_RV1(256, 32, 256, 8, 6, 1)
+    PPF_RV1(512, 8, 512, 8, 4, 1) PPF_RV1(512, 8, 256, 8, 4, 1)
+    PPF_RV1(512, 16, 512, 8, 4, 1) PPF_RV1(512, 32, 512, 4, 10, 1)
+    PPF_RV1(1024, 8, 512, 4, 4, 1) PPF_RV1(1024, 16, 512, 2, 10, 1)
+    PPF_RV1(2048, 4, 512, 2, 4, 1)
     return idx;
 }
 

@@ -52,7 +52,8 @@ template <class C>
 KernelEntry entry()
 {
     static char name[64];
-    std::snprintf(name, sizeof(name), "ring:nt%d:rb%d:nch%d:b%d", C::NT, C::RB, C::NCH, C::MINB);
+    std::snprintf(name, sizeof(name), "ring:nt%d:rb%d:nch%d:b%d%s", C::NT, C::RB, C::NCH, C::MINB,
+                  C::CPT == 1 ? ":c1" : "");
     KernelEntry e;
     e.name = name;
     e.prepare = prepare_ring<C>;
@@ -66,9 +67,15 @@ KernelEntry entry()
 }  // namespace ring_detail
 }  // namespace ppf
 
-// Walk a variant list: PPF_RV(NN, TT, NT, RB, NCH, MINB) entries for one input type.
+// Walk a variant list: PPF_RV(NN, TT, NT, RB, NCH, MINB) entries for one input type
+// (a channel pair per FIR thread); PPF_RV1: the same with one channel per thread.
 #define PPF_RV(NN, TT, NT, RB, NCH, MINB)                                                      \
     if (N == NN && T == TT) {                                                                  \
         if (idx == want && out) *out = ring_detail::entry<RingCfg<NN, TT, In, NT, RB, NCH, MINB>>(); \
+        ++idx;                                                                                 \
+    }
+#define PPF_RV1(NN, TT, NT, RB, NCH, MINB)                                                     \
+    if (N == NN && T == TT) {                                                                  \
+        if (idx == want && out) *out = ring_detail::entry<RingCfg<NN, TT, In, NT, RB, NCH, MINB, 1>>(); \
         ++idx;                                                                                 \
     }
