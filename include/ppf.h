@@ -307,6 +307,30 @@ const char* ppf_variant_name(int N, int T, ppf_dtype_t dtype, int i);
 /* Kernel launches this library has issued since load (for reports). */
 int64_t ppf_launch_count(void);
 
+/* Window of the prototype low-pass filter (Section 2). */
+typedef enum {
+    PPF_WINDOW_HAMMING = 0,    /* 0.54 - 0.46 cos(2 pi n / (L-1)) */
+    PPF_WINDOW_KAISER = 1      /* I0(beta sqrt(1 - (2n/(L-1) - 1)^2)) / I0(beta) */
+} ppf_window_t;
+
+/*
+ * ppf_design_coeffs -- windowed-sinc prototype filter for an N-channel,
+ * T-tap bank (Section 2: a truncated sinc shaped by a window; the paper names
+ * a Kaiser window and gives no parameter, so beta is the caller's).  Host
+ * only, no device work; needs no GPU.
+ *   N, T      channels (>= 1) and taps per channel (>= 1); L = N*T.
+ *   window    PPF_WINDOW_HAMMING or PPF_WINDOW_KAISER.
+ *   beta      Kaiser shape parameter (>= 0; ignored for Hamming).
+ *   h_out     caller-owned host array of N*T floats, written as
+ *             h[n] = sinc((n - (L-1)/2) / N) * w[n], sinc(x) = sin(pi x)/(pi x),
+ *             computed in FP64 and rounded to FP32; no normalisation.  The
+ *             layout is the one ppf_plan_create takes (h[t*N + c], t = n / N).
+ * I0 is evaluated by its power series.  Returns PPF_ERR_INVALID_ARG for a
+ * NULL h_out, N < 1, T < 1, an unknown window or a negative or non-finite
+ * beta.
+ */
+ppf_status_t ppf_design_coeffs(int N, int T, ppf_window_t window, double beta, float* h_out);
+
 #ifdef __cplusplus
 }
 #endif

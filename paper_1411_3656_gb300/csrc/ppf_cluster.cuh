@@ -76,7 +76,7 @@ struct ClusterCfg {
     static constexpr int X_SLOTS = RB * K2 * RS1;
     static constexpr int XBYTES = RB * K2 * N1 * 8;  // bytes each CTA receives per block
     static constexpr int SMEM = RING_BYTES + (A_SLOTS + 2 * X_SLOTS) * 8 + (NCH + 4) * 8;
-    static_assert(P >= 2 && P <= 8, "portable cluster sizes");
+    static_assert(P >= 2 && P <= 16, "cluster sizes 2..16 (above 8 needs the non-portable opt-in)");
     static_assert(CPT == 1 || CPT == 2, "one channel or a pair per thread");
     static_assert(UNITS % NT == 0 || NT % UNITS == 0, "FIR units must tile the threads");
     static_assert(C1 >= 2 && C1 % 2 == 0 && (C1 * BPS) % 16 == 0, "TMA box rows must be 16-byte multiples");

@@ -32,6 +32,12 @@ static int variants_impl(int N, int T, int want, KernelEntry* out)
     PPF_CV(4096, 4, 8, 64, 128, 4, 3, 2)
     PPF_CV(4096, 8, 8, 64, 128, 2, 6, 2)
     PPF_CV(4096, 16, 8, 64, 128, 2, 10, 2)
+    // 16-CTA clusters (non-portable size): 256 channels per CTA
+    PPF_CV(4096, 32, 16, 64, 128, 4, 10, 2) PPF_CV1(4096, 32, 16, 64, 256, 8, 6, 1)
+    PPF_CV1(4096, 32, 16, 64, 256, 4, 10, 1)
+    PPF_CV(4096, 16, 16, 64, 128, 4, 6, 2) PPF_CV1(4096, 16, 16, 64, 256, 8, 4, 1)
+    PPF_CV(4096, 8, 16, 64, 128, 4, 4, 2)
+    PPF_CV(2048, 32, 16, 64, 128, 4, 10, 2)
     return idx;
 }
 

@@ -72,6 +72,10 @@ cudaError_t prepare_cluster(PlanView& p)
     if (!encode_fn()) return cudaErrorNotSupported;
     cudaError_t e = cudaFuncSetAttribute(ppf_cluster_kernel<C>, cudaFuncAttributeMaxDynamicSharedMemorySize, C::SMEM);
     if (e != cudaSuccess) return e;
+    if (C::P > 8) {
+        e = cudaFuncSetAttribute(ppf_cluster_kernel<C>, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
+        if (e != cudaSuccess) return e;
+    }
     cudaLaunchAttribute attr[1];
     cudaLaunchConfig_t cfg = launch_config<C>(C::P * p.sms, nullptr, attr);
     int ncl = 0;

@@ -17,6 +17,9 @@ int cluster_variants_c16(int N, int T, int want, KernelEntry* out);
 int ring_variants_ci8(int N, int T, int want, KernelEntry* out);
 int cluster_variants_ci8(int N, int T, int want, KernelEntry* out);
 int split_variants_c32(int N, int T, int want, KernelEntry* out);
+int twopass_variants_c32(int N, int T, int want, KernelEntry* out);
+int twopass_variants_c16(int N, int T, int want, KernelEntry* out);
+int twopass_variants_ci8(int N, int T, int want, KernelEntry* out);
 static int no_variants(int, int, int, KernelEntry*) { return 0; }
 
 using VariantFn = int (*)(int, int, int, KernelEntry*);
@@ -24,9 +27,10 @@ using VariantFn = int (*)(int, int, int, KernelEntry*);
 // Number of variants for (N, T, dtype); fills *out with variant `want` if it exists.
 int variants(int N, int T, int dtype, int want, KernelEntry* out)
 {
-    static const VariantFn lists[3][3] = {{ring_variants_c32, cluster_variants_c32, split_variants_c32},
-                                          {ring_variants_c16, cluster_variants_c16, no_variants},
-                                          {ring_variants_ci8, cluster_variants_ci8, no_variants}};
+    static const VariantFn lists[3][4] = {
+        {ring_variants_c32, cluster_variants_c32, split_variants_c32, twopass_variants_c32},
+        {ring_variants_c16, cluster_variants_c16, no_variants, twopass_variants_c16},
+        {ring_variants_ci8, cluster_variants_ci8, no_variants, twopass_variants_ci8}};
     if (dtype < 0 || dtype > 2) return 0;
     int n = 0;
     for (VariantFn f : lists[dtype]) {

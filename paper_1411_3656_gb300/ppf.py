@@ -33,7 +33,7 @@ EXPORTS = ("ppf_plan_create", "ppf_plan_destroy", "ppf_execute", "ppf_execute_ho
            "ppf_variant_name", "ppf_execute_noalloc", "ppf_batch_create", "ppf_batch_execute",
            "ppf_batch_launches", "ppf_batch_destroy", "ppf_server_create", "ppf_server_admit",
            "ppf_server_release", "ppf_server_submit", "ppf_server_submit_many", "ppf_server_tick", "ppf_server_position",
-           "ppf_server_info", "ppf_server_destroy")
+           "ppf_server_info", "ppf_server_destroy", "ppf_design_coeffs")
 
 
 class PPFJob(ctypes.Structure):
@@ -95,6 +95,7 @@ def load(path: str | None = None):
             "ppf_server_position": ([vp, i32, ctypes.POINTER(i64), ctypes.POINTER(i64)], i32),
             "ppf_server_info": ([vp, ctypes.POINTER(ctypes.c_size_t), ctypes.POINTER(i32), ctypes.POINTER(i32)], i32),
             "ppf_server_destroy": ([vp], i32),
+            "ppf_design_coeffs": ([i32, i32, i32, ctypes.c_double, ctypes.POINTER(ctypes.c_float)], i32),
         }
         for name, (args, res) in sig.items():
             fn = getattr(lib, name)
@@ -195,6 +196,21 @@ def ppf_execute_noalloc(N: int, T: int, dtype: str, d_h: int, d_in: int, d_out: 
                         stream: int = 0) -> int:
     """No-allocation PPF (see include/ppf.h): coefficients as a device FP32 array."""
     return load().ppf_execute_noalloc(int(N), int(T), DTYPES[dtype], d_h, d_in, d_out, int(n_spectra), stream)
+
+
+WINDOWS = {"hamming": 0, "kaiser": 1}
+
+
+def ppf_design_coeffs(N: int, T: int, window: str = "kaiser", beta: float = 8.0):
+    """Windowed-sinc prototype filter h[t*N + c] (float32 numpy array of N*T)."""
+    import numpy as np
+    if window not in WINDOWS:
+        raise ValueError(f"window must be one of {sorted(WINDOWS)}")
+    h = np.empty(max(0, int(N) * int(T)), dtype=np.float32)
+    st = load().ppf_design_coeffs(int(N), int(T), WINDOWS[window], float(beta),
+                                  h.ctypes.data_as(ctypes.POINTER(ctypes.c_float)))
+    _check(st, "ppf_design_coeffs")
+    return h
 
 
 def flag_variant(i: int) -> int:

@@ -236,3 +236,34 @@ def test_every_variant(ppf, N, T, dtype):
         Y, kern = _run(ppf, xs, h, N, T, S, dtype=dtype, flags=ppf.flag_variant(i))
         assert kern == ppf.ppf_variant_name(N, T, dtype, i)
         assert synth.rel_l2(Y, ref) <= TOL32, kern
+
+
+CHUNKED_CELLS = [(512, 32), (2048, 8), (4096, 8), (4096, 32)]
+
+
+@pytest.mark.parametrize("N,T", CHUNKED_CELLS)
+def test_scratch_variants_across_chunks(ppf, N, T):
+    """Variants that run through plan scratch (two-pass chunk buffer, split
+    exchange rows) on streams long enough to cross several chunk boundaries;
+    spectra around every 256-spectrum boundary, and the ends, against the oracle."""
+    import torch
+    S = 3 * (64 << 20) // (N * 8) // 2 + 37
+    x, h = _rand(N, T, S, 3000 + N + T)
+    rows = sorted({0, 1, S - 2, S - 1} | {r for m in range(256, S, 256) for r in (m - 1, m, m + 1) if r < S})
+    rows = np.asarray(rows, dtype=np.int64)
+    ref = oracle.ppf_rows(x, h, N, T, rows)
+    xd = _dev(x)
+    tested = 0
+    for i in range(ppf.ppf_variant_count(N, T, "c32")):
+        name = ppf.ppf_variant_name(N, T, "c32", i)
+        if not name.startswith(("twopass", "split")):
+            continue
+        plan = ppf.Plan(N, T, h, "c32", ppf.flag_variant(i))
+        Y = plan(xd, n_spectra=S)
+        torch.cuda.synchronize()
+        got = Y[torch.from_numpy(rows).to("cuda")].cpu().numpy()
+        assert synth.rel_l2(got, ref) <= TOL32, name
+        plan.close()
+        del Y
+        tested += 1
+    assert tested > 0
