@@ -307,6 +307,19 @@ const char* ppf_variant_name(int N, int T, ppf_dtype_t dtype, int i);
 /* Kernel launches this library has issued since load (for reports). */
 int64_t ppf_launch_count(void);
 
+/*
+ * ppf_check_timeout -- failure-detection self-check (no paper counterpart).
+ * One warp on the device waits on an mbarrier that nothing completes, through
+ * the same bounded wait every PPF kernel uses for its copies and exchanges,
+ * with a limit of limit_us microseconds (1..1000000) instead of the kernels'
+ * 2 s; the wait gives up and raises the mapped error word.  Synchronises
+ * `stream` (cudaStream_t as void*).  Returns PPF_ERR_TIMEOUT when the wait ran
+ * out and was reported (the expected result), PPF_OK if it was not reported,
+ * PPF_ERR_INVALID_ARG for a limit out of range, PPF_ERR_CUDA on a CUDA error.
+ * The device stays usable afterwards.
+ */
+ppf_status_t ppf_check_timeout(unsigned limit_us, void* stream);
+
 /* Window of the prototype low-pass filter (Section 2). */
 typedef enum {
     PPF_WINDOW_HAMMING = 0,    /* 0.54 - 0.46 cos(2 pi n / (L-1)) */

@@ -1,0 +1,46 @@
+// Failure-detection self-check: the device-side bounded wait, made to run out.
+#include <cuda_runtime.h>
+
+#include "../../include/ppf.h"
+#include "ppf_launch.h"
+#include "ppf_ptx.cuh"
+
+namespace {
+
+// One warp waits on an mbarrier that nothing arrives on, with the same bounded
+// wait the PPF kernels use, and reports the give-up through the error word.
+__global__ void wait_timeout_kernel(uint64_t limit_ns, int* err)
+{
+    __shared__ uint64_t bar;
+    if (threadIdx.x == 0) {
+        ppf::mbar_init(&bar, 1);
+        ppf::fence_mbar_init();
+    }
+    __syncwarp();
+    const bool ok = ppf::mbar_wait_bounded(&bar, 0, limit_ns);
+    if (__any_sync(0xffffffffu, !ok) && threadIdx.x == 0) atomicExch(err, 1);
+}
+
+}  // namespace
+
+extern "C" ppf_status_t ppf_check_timeout(unsigned limit_us, void* stream)
+{
+    if (limit_us < 1 || limit_us > 1000000) return PPF_ERR_INVALID_ARG;
+    int* h_err = nullptr;
+    int* d_err = nullptr;
+    cudaError_t e = cudaHostAlloc((void**)&h_err, sizeof(int), cudaHostAllocMapped);
+    if (e != cudaSuccess) return PPF_ERR_OUT_OF_MEMORY;
+    *h_err = 0;
+    e = cudaHostGetDevicePointer((void**)&d_err, h_err, 0);
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    if (e == cudaSuccess) {
+        wait_timeout_kernel<<<1, 32, 0, st>>>((uint64_t)limit_us * 1000u, d_err);
+        ppf::note_launch();
+        e = cudaGetLastError();
+    }
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    const int flagged = *(volatile int*)h_err;
+    cudaFreeHost(h_err);
+    if (e != cudaSuccess) return PPF_ERR_CUDA;
+    return flagged ? PPF_ERR_TIMEOUT : PPF_OK;
+}

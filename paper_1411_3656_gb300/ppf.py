@@ -33,7 +33,7 @@ EXPORTS = ("ppf_plan_create", "ppf_plan_destroy", "ppf_execute", "ppf_execute_ho
            "ppf_variant_name", "ppf_execute_noalloc", "ppf_batch_create", "ppf_batch_execute",
            "ppf_batch_launches", "ppf_batch_destroy", "ppf_server_create", "ppf_server_admit",
            "ppf_server_release", "ppf_server_submit", "ppf_server_submit_many", "ppf_server_tick", "ppf_server_position",
-           "ppf_server_info", "ppf_server_destroy", "ppf_design_coeffs")
+           "ppf_server_info", "ppf_server_destroy", "ppf_design_coeffs", "ppf_check_timeout")
 
 
 class PPFJob(ctypes.Structure):
@@ -96,6 +96,7 @@ def load(path: str | None = None):
             "ppf_server_info": ([vp, ctypes.POINTER(ctypes.c_size_t), ctypes.POINTER(i32), ctypes.POINTER(i32)], i32),
             "ppf_server_destroy": ([vp], i32),
             "ppf_design_coeffs": ([i32, i32, i32, ctypes.c_double, ctypes.POINTER(ctypes.c_float)], i32),
+            "ppf_check_timeout": ([ctypes.c_uint, vp], i32),
         }
         for name, (args, res) in sig.items():
             fn = getattr(lib, name)
@@ -196,6 +197,11 @@ def ppf_execute_noalloc(N: int, T: int, dtype: str, d_h: int, d_in: int, d_out: 
                         stream: int = 0) -> int:
     """No-allocation PPF (see include/ppf.h): coefficients as a device FP32 array."""
     return load().ppf_execute_noalloc(int(N), int(T), DTYPES[dtype], d_h, d_in, d_out, int(n_spectra), stream)
+
+
+def ppf_check_timeout(limit_us: int = 1000, stream=None) -> int:
+    """Run the device bounded-wait self-check; returns the status (PPF_ERR_TIMEOUT expected)."""
+    return load().ppf_check_timeout(int(limit_us), _stream_ptr(stream))
 
 
 WINDOWS = {"hamming": 0, "kaiser": 1}
