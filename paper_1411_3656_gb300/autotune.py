@@ -40,6 +40,42 @@ def time_variant(ppf, torch, N, T, dtype, flags, x, y, S, reps=10):
     return e0.elapsed_time(e1) / reps, name
 
 
+def reindex_line(ppf, ln: str):
+    """Re-resolve an entry's variant index from its name against the compiled
+    variant lists (they change when variants are added); None if the name is gone."""
+    import re
+    m = re.match(r'PPF_TUNED\((\d+), (\d+), (\d+), (\d+), "([^"]+)"\)(.*)', ln)
+    if not m:
+        return None
+    N, T, d, _, name, rest = int(m[1]), int(m[2]), int(m[3]), int(m[4]), m[5], m[6]
+    dtype = {v: k for k, v in ppf.DTYPES.items()}[d]
+    for i in range(ppf.ppf_variant_count(N, T, dtype)):
+        if ppf.ppf_variant_name(N, T, dtype, i) == name:
+            return f'PPF_TUNED({N}, {T}, {d}, {i}, "{name}"){rest}'
+    return None
+
+
+def reindex_file(path: str) -> int:
+    """Host-only: rewrite a tuned table with every index re-resolved by name."""
+    sys.path.insert(0, os.path.dirname(HERE))
+    from paper_1411_3656_gb300 import build, ppf
+    build.build()
+    ppf.load()
+    head, body = [], []
+    for ln in open(path):
+        ln = ln.rstrip("\n")
+        if ln.startswith("PPF_TUNED("):
+            new = reindex_line(ppf, ln)
+            if new:
+                body.append(new)
+        else:
+            head.append(ln)
+    with open(path, "w") as f:
+        for ln in head + body:
+            f.write(ln + "\n")
+    return len(body)
+
+
 def main(argv=None):
     ap = argparse.ArgumentParser()
     ap.add_argument("--out", default=DEFAULT_OUT)
@@ -47,7 +83,12 @@ def main(argv=None):
     ap.add_argument("--cells", default="")
     ap.add_argument("--dtype", default="c32", choices=("c32", "c16", "ci8"))
     ap.add_argument("--seconds", type=float, default=1.0)
+    ap.add_argument("--reindex", action="store_true",
+                    help="only re-resolve the table's variant indices by name (no GPU needed)")
     args = ap.parse_args(argv)
+    if args.reindex:
+        print(f"{reindex_file(args.out)} entries", flush=True)
+        return 0
 
     import numpy as np
     import torch
@@ -93,7 +134,9 @@ def main(argv=None):
                 parts = ln[len("PPF_TUNED("):].split(",")
                 n, t, d = int(parts[0]), int(parts[1]), int(parts[2])
                 if not (d == dt and (n, t) in keep):
-                    old.append(ln.rstrip("\n"))
+                    new = reindex_line(ppf, ln.rstrip("\n"))
+                    if new:
+                        old.append(new)
     with open(args.out, "w") as f:
         f.write("// Written by paper_1411_3656_gb300/autotune.py on a GB300: fastest variant per\n"
                 "// (N, T, dtype) as PPF_TUNED(N, T, dtype, variant index, variant name).\n")

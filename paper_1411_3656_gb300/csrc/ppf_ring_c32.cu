@@ -15,6 +15,10 @@ static int variants_impl(int N, int T, int want, KernelEntry* out)
     PPF_RV1(512, 16, 512, 8, 4, 1) PPF_RV1(512, 32, 512, 4, 10, 1)
     PPF_RV1(1024, 8, 512, 4, 4, 1) PPF_RV1(1024, 16, 512, 2, 10, 1)
     PPF_RV1(2048, 4, 512, 2, 4, 1)
+    PPF_RV1(2048, 8, 512, 1, 9, 1) PPF_RV1(1024, 8, 512, 2, 6, 1) PPF_RV1(512, 16, 512, 4, 6, 1)
+    // two CTAs per SM
+    PPF_RV1(512, 8, 256, 4, 4, 2) PPF_RV1(1024, 4, 256, 2, 4, 2)
+    PPF_RV1(256, 16, 256, 8, 4, 2) PPF_RV1(256, 8, 256, 8, 4, 2)
     return idx;
 }
 
