@@ -12,6 +12,7 @@ static int variants_impl(int N, int T, int want, KernelEntry* out)
     PPF_CV(4096, 4, 8, 32, 256, 4, 3, 1) PPF_CV(4096, 8, 8, 32, 256, 4, 4, 1)
     PPF_CV(4096, 16, 8, 32, 256, 4, 6, 1) PPF_CV(4096, 32, 8, 32, 256, 4, 10, 1)
     PPF_CV(2048, 8, 4, 32, 256, 4, 4, 1) PPF_CV(2048, 16, 4, 32, 256, 4, 6, 1)
+#include "ppf_cluster_reduced.inc"
     return idx;
 }
 

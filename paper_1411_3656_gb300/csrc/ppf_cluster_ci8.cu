@@ -8,6 +8,7 @@ static int variants_impl(int N, int T, int want, KernelEntry* out)
 {
     int idx = 0;
 #include "ppf_cluster_table.inc"
+#include "ppf_cluster_reduced.inc"
     return idx;
 }
 

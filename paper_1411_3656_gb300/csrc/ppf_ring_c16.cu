@@ -10,6 +10,7 @@ static int variants_impl(int N, int T, int want, KernelEntry* out)
 #include "ppf_ring_table.inc"
     PPF_RV(512, 32, 256, 8, 6, 1) PPF_RV(1024, 8, 256, 4, 5, 1) PPF_RV(1024, 16, 256, 4, 6, 1)
     PPF_RV(1024, 16, 256, 4, 7, 1) PPF_RV(2048, 8, 256, 2, 6, 1)
+#include "ppf_ring_reduced.inc"
     return idx;
 }
 

@@ -267,3 +267,38 @@ def test_scratch_variants_across_chunks(ppf, N, T):
         del Y
         tested += 1
     assert tested > 0
+
+
+SWEEP_CELLS = [(N, T) for N in (256, 512, 1024, 2048, 4096) for T in (4, 8, 16, 32)]
+
+
+@pytest.fixture(scope="module")
+def second_of_data():
+    """One second of 6.5 GB/s complex64 (8.125e8 samples), shared by every sweep
+    cell (each reads its prefix of (S+T-1)*N samples), on the host and the device."""
+    x = synth.stream(int(synth.REALTIME_SAMPLES_PER_S), 1024, synth.BASE_SEED + 11)
+    xd = _dev(x)
+    yield x, xd
+    del xd
+
+
+@pytest.mark.parametrize("N,T", SWEEP_CELLS)
+def test_full_size_sweep_cell_sampled(ppf, second_of_data, N, T):
+    """Every cell of the real-time sweep at full size, with the tuned default
+    kernel and launch configuration the benchmark times: 272 spectra (the first
+    8, the last 8, 256 seeded) against the oracle."""
+    import torch
+    x, xd = second_of_data
+    S = synth.spectra_for(x.shape[0], N, T)
+    h = synth.hamming_sinc(N, T)
+    plan = ppf.Plan(N, T, h)
+    Y = plan(xd[: synth.samples_for(S, N, T)], n_spectra=S)
+    torch.cuda.synchronize()
+    rows = synth.sample_rows(S, count=256)
+    got = Y[torch.from_numpy(rows).to("cuda")].cpu().numpy()
+    kern = plan.kernel
+    del Y
+    plan.close()
+    torch.cuda.empty_cache()
+    ref = oracle.ppf_rows(x, h, N, T, rows)
+    assert synth.rel_l2(got, ref) <= TOL32, kern
