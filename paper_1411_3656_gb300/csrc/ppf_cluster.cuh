@@ -414,8 +414,13 @@ ppf_cluster_kernel(const __grid_constant__ CUtensorMap xmap, const PpfWork wl, c
                     }
                 }
                 // A failed wait is recorded and the cluster keeps its schedule (no
-                // early exit, so no CTA waits on one that has left).
-                if (__syncthreads_or(!ok)) failed = true;
+                // early exit, so no CTA waits on one that has left); the flag
+                // spreads over the CTA at the barrier after the FIR.  Every thread
+                // waits for the chunks itself, so no barrier is needed here, except
+                // after block 0, whose stage-1 reads of A no stage-2 barrier has
+                // yet ordered before this block's FIR writes.
+                if (!ok) failed = true;
+                if (b == 1) __syncthreads();
 
                 // 1. FIR over the ring
 #pragma unroll
@@ -471,7 +476,7 @@ ppf_cluster_kernel(const __grid_constant__ CUtensorMap xmap, const PpfWork wl, c
                         for (int i = 0; i < RBT; ++i) A[(i0 + i) * C::RSB + l] = a[i];
                     }
                 }
-                __syncthreads();
+                if (__syncthreads_or(failed)) failed = true;
                 if (tid == 0 && !failed && issued < nchunks && issued == b + NCH) {
                     issue(issued);
                     ++issued;
@@ -483,19 +488,18 @@ ppf_cluster_kernel(const __grid_constant__ CUtensorMap xmap, const PpfWork wl, c
                 const int gb = gbase + b, par = gb & 1;
                 if (tid == 0) mbar_arrive_expect_tx(&xfull[par], (uint32_t)C::XBYTES);
                 stage1_upto_last<C>(A, tw1, so);
-                // the owners have finished reading X[par] of exchange gb-2
-                bool okf = true;
-                if (gb >= 2 && !failed) okf = mbar_wait_bounded(&xfree[par], (uint32_t)(((gb >> 1) - 1) & 1));
-                if (__syncthreads_or(!okf)) failed = true;
+                // the owners have finished reading X[par] of exchange gb-2 (each
+                // thread waits before its own sends)
+                if (gb >= 2 && !failed && !mbar_wait_bounded(&xfree[par], (uint32_t)(((gb >> 1) - 1) & 1)))
+                    failed = true;
                 stage1_pass<C, fft_npass(C::N2) - 1>(A, tw1, so, (uint32_t)(par * C::X_SLOTS * 8),
                                                      (uint32_t)(par * 8));
             }
             if (b >= 1) {
                 // 4. block b-1: once every byte of X[par] is here, N1-point DFTs and store
                 const int bp = b - 1, gb = gbase + bp, par = gb & 1;
-                bool okf = true;
-                if (!failed) okf = mbar_wait_bounded(&xfull[par], (uint32_t)((gb >> 1) & 1));
-                if (__syncthreads_or(!okf)) failed = true;
+                // each thread waits before its own reads of X[par]
+                if (!failed && !mbar_wait_bounded(&xfull[par], (uint32_t)((gb >> 1) & 1))) failed = true;
                 const int64_t s0 = s_lo + (int64_t)bp * RB;
                 const int rows = (int)(s_hi - s0 < RB ? s_hi - s0 : RB);
                 stage2<C>(X + par * C::X_SLOTS, tw2, Y + s0 * N, rows, rank, [&] {
@@ -514,10 +518,11 @@ ppf_cluster_kernel(const __grid_constant__ CUtensorMap xmap, const PpfWork wl, c
         cbase += nchunks;
         gbase += nb;
     }
+    const bool any_failed = __syncthreads_or(failed);
     // no CTA leaves while a peer may still store into its shared memory
     cluster_arrive_release();
     cluster_wait_acquire();
-    if (failed && tid == 0) atomicExch(err, 1);
+    if (any_failed && tid == 0) atomicExch(err, 1);
 }
 
 }  // namespace ppf
