@@ -16,13 +16,9 @@ static int variants_impl(int N, int T, int want, KernelEntry* out)
     PPF_CV1(512, 32, 2, 32, 256, 8, 6, 1)
     PPF_CV1(1024, 16, 4, 64, 256, 8, 4, 1) PPF_CV1(1024, 16, 4, 32, 256, 8, 4, 1)
     PPF_CV1(1024, 32, 4, 64, 256, 4, 10, 1) PPF_CV1(1024, 32, 4, 32, 256, 8, 6, 1)
-    PPF_CV1(2048, 8, 4, 64, 512, 8, 3, 1) PPF_CV1(2048, 8, 8, 64, 256, 8, 3, 1)
-    PPF_CV1(2048, 16, 4, 64, 512, 4, 6, 1) PPF_CV1(2048, 16, 8, 64, 256, 8, 4, 1)
+    PPF_CV1(2048, 8, 8, 64, 256, 8, 3, 1)
+    PPF_CV1(2048, 16, 8, 64, 256, 8, 4, 1)
     PPF_CV1(2048, 32, 8, 64, 256, 4, 10, 1)
-    PPF_CV1(4096, 4, 8, 64, 512, 8, 3, 1)
-    PPF_CV1(4096, 8, 8, 128, 512, 8, 3, 1) PPF_CV1(4096, 8, 8, 64, 512, 4, 4, 1)
-    PPF_CV1(4096, 16, 8, 128, 512, 4, 6, 1) PPF_CV1(4096, 16, 8, 64, 512, 4, 6, 1)
-    PPF_CV1(4096, 32, 8, 128, 512, 4, 10, 1) PPF_CV1(4096, 32, 8, 64, 512, 4, 10, 1)
     // two CTAs per SM: one CTA's barriers and exchange waits overlap the other's work
     PPF_CV1(512, 32, 4, 32, 128, 4, 10, 2)
     PPF_CV(1024, 16, 4, 64, 128, 4, 6, 2) PPF_CV1(1024, 16, 4, 64, 128, 4, 6, 2)
