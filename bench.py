@@ -52,6 +52,8 @@ def parse():
     ap.add_argument("--cells", default="", help="comma list N:T to restrict the sweep")
     ap.add_argument("--seconds", type=float, default=1.0, help="seconds of 6.5 GB/s data per cell")
     ap.add_argument("--dtype", choices=("c32", "c16", "ci8"), default="c32")
+    ap.add_argument("--out-dtype", choices=("c64", "f16"), default="c64",
+                    help="output bins: complex64, or FP16 (I, Q) pairs (plan flag PPF_FLAG_OUT_F16)")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-unfused", action="store_true",
@@ -349,6 +351,8 @@ def run_ours(args):
     for N, T in cells:
         S = spectra_of(args, N, T)
         flags = ppf.flag_variant(args.variant) if args.variant >= 0 else 0
+        if args.out_dtype == "f16":
+            flags |= ppf.FLAG_OUT_F16
         plans.append((N, T, S, ppf.Plan(N, T, synth.hamming_sinc(N, T), dtype, flags)))
     stream = torch.cuda.current_stream(dev)
     sp = stream.cuda_stream
@@ -392,11 +396,12 @@ def run_ours(args):
 
     samples_step = sum(S * N for N, T, S, _ in plans)
     value = job_msamples_per_s(samples_step, args.steps, world, elapsed_ms)
+    out_bytes = 4 if args.out_dtype == "f16" else 8
     hbm, peak_src = peaks()
     cell_rows, tot_bytes, tot_kernel_ms = [], 0, 0.0
     for i, (N, T, S, plan) in enumerate(plans):
         ms = statistics.mean(evs[k][i][0].elapsed_time(evs[k][i][1]) for k in range(args.steps))
-        b = metrics.algorithmic_bytes(N, T, S, dtype)
+        b = metrics.algorithmic_bytes(N, T, S, dtype, out_bytes)
         tot_bytes += b
         tot_kernel_ms += ms
         gbs = b / (ms / 1e3) / 1e9
@@ -411,7 +416,7 @@ def run_ours(args):
 
     # e2e through the public host-buffer entry point (pinned memory, copies inside)
     e2e = None
-    if not args.no_e2e:
+    if not args.no_e2e and args.out_dtype == "c64":  # host-buffer entry point: complex64 output only
         xh = torch.from_numpy(x_host).pin_memory()
         yh = torch.empty(s_max, dtype=torch.complex64).pin_memory()
         bps = metrics.IN_BYTES[dtype]
@@ -436,7 +441,8 @@ def run_ours(args):
         del xh, yh
 
     unfused = None
-    if rank == 0 and world == 1 and not args.no_unfused and args.workload == "realtime_sweep":
+    if (rank == 0 and world == 1 and not args.no_unfused and args.workload == "realtime_sweep"
+            and args.out_dtype == "c64"):
         unfused = unfused_comparison(args, plans, x_dev, y_dev, cell_rows, stream, dev)
 
     cpu = None
@@ -450,18 +456,19 @@ def run_ours(args):
             "value": value, "unit": "Msamples/s", "n_gpus": world, "steps": args.steps,
             "warmup": max(3, args.warmup), "ms_per_step": elapsed_ms / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-            "dtype": {"c32": "f32", "c16": "f16-in/f32", "ci8": "i8-in/f32"}[dtype], "data": "synthetic",
+            "dtype": {"c32": "f32", "c16": "f16-in/f32", "ci8": "i8-in/f32"}[dtype]
+            + ("/f16-out" if args.out_dtype == "f16" else ""), "data": "synthetic",
             "config": {"workload": args.workload + (" (1 s of 6.5 GB/s complex64 per (N,T) cell)"
                                                    if args.workload == "realtime_sweep" else " (N=256,T=8,S=1024)"),
                        "cells": [f"{N}:{T}" for N, T in cells], "seconds_per_cell": args.seconds,
-                       "input": dtype, "l2": "inputs larger than L2 (no flush needed)"
+                       "input": dtype, "output": args.out_dtype, "l2": "inputs larger than L2 (no flush needed)"
                        if samples_step * 8 > 129e6 else "L2-resident",
                        "parallelism": f"replicas x{world}"},
             "x_realtime": data_s * args.steps / (elapsed_ms / 1e3),
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s",
                          "frac": achieved / hbm,
                          "traffic": measured_traffic(args.workload, dtype)
-                         if (not args.cells and args.seconds == 1.0) else None,
+                         if (not args.cells and args.seconds == 1.0 and args.out_dtype == "c64") else None,
                          "algorithmic_bytes_per_step": tot_bytes,
                          "kernel": "fused FIR+FFT (all cells, byte-weighted)", "peak_source": peak_src},
             "clocks": clock,

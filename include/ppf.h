@@ -24,7 +24,8 @@
  *     else is PPF_ERR_UNSUPPORTED.  int8 input needs N >= 8.
  *   - Samples: PPF_IN_C32 = float2 (I, Q) 8 bytes; PPF_IN_C16 = two IEEE
  *     half values (I, Q) 4 bytes; PPF_IN_CI8 = two signed 8-bit integers
- *     (I, Q) 2 bytes, used unscaled.  Output is always float2 (complex64).
+ *     (I, Q) 2 bytes, used unscaled.  Output is float2 (complex64), or FP16
+ *     (I, Q) pairs with PPF_FLAG_OUT_F16.
  *   - Arithmetic: FIR and FFT accumulate in FP32.  h is FP32 for C32 input
  *     and is rounded to FP16 for C16 / CI8 input.
  *   - Device buffers belong to the caller, must be 16-byte aligned
@@ -73,6 +74,13 @@ typedef enum {
 #define PPF_FLAG_NONE 0u
 #define PPF_FLAG_FIR_ONLY 1u   /* test hook: write the FIR output y instead of Y */
 #define PPF_FLAG_GENERIC 2u    /* always use the general kernel (runtime T, any size) */
+/* Output bins as FP16 (I, Q) pairs (4 bytes per bin, rounded to nearest)
+ * instead of complex64: a quarter less HBM traffic for complex64 input, 40%
+ * less for int8 I/Q.  Bins beyond +-65504 become +-inf; the arithmetic stays
+ * FP32.  Supported by ppf_execute and ppf_batch_*; ppf_execute_host,
+ * ppf_stream_open and ppf_server_admit return PPF_ERR_UNSUPPORTED for such a
+ * plan, and so does ppf_plan_create together with PPF_FLAG_FIR_ONLY. */
+#define PPF_FLAG_OUT_F16 4u
 /* Force specialised kernel variant i (0-based) of ppf_variant_count(N, T, dtype)
  * instead of the tuned default; used by the autotuner. */
 #define PPF_FLAG_VARIANT(i) ((((unsigned)(i) + 1u) & 0xFFu) << 8)
@@ -105,7 +113,8 @@ ppf_status_t ppf_plan_destroy(ppf_plan_t plan);
  *   d_in       device input, (n_spectra + T - 1) * N samples of the plan's
  *              dtype, one contiguous stream (sample n = r*N + c is row r,
  *              channel c).  Read only.
- *   d_out      device output, n_spectra * N complex64, row-major [s][k].
+ *   d_out      device output, n_spectra * N bins, row-major [s][k]: complex64,
+ *              or FP16 (I, Q) pairs for a plan made with PPF_FLAG_OUT_F16.
  *   n_spectra  number of output spectra S >= 0 (0 enqueues nothing).
  *   stream     cudaStream_t as void*.
  * One launch of the fused FIR+FFT kernel: each input sample is read from
@@ -191,7 +200,8 @@ typedef struct ppf_batch_s* ppf_batch_t;
 typedef struct {
     ppf_plan_t plan;     /* the job's plan (not owned; must outlive the batch) */
     const void* d_in;    /* device input, (n_spectra + T - 1) * N samples, 16-byte aligned */
-    void* d_out;         /* device output, n_spectra * N complex64, 16-byte aligned */
+    void* d_out;         /* device output, n_spectra * N bins (complex64, or FP16 pairs with
+                            PPF_FLAG_OUT_F16), 16-byte aligned */
     int64_t n_spectra;   /* spectra of this job, >= 0 */
 } ppf_job_t;
 

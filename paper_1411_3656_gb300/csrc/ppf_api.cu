@@ -21,7 +21,7 @@ namespace ppf {
 static std::atomic<int64_t> g_launches{0};
 void note_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
 
-KernelEntry select_fast_entry(int N, int T, int dtype, int variant);  // ppf_select.cu
+KernelEntry select_fast_entry(int N, int T, int dtype, int variant, int out_f16);  // ppf_select.cu
 
 }  // namespace ppf
 
@@ -157,7 +157,8 @@ ppf_status_t ppf_plan_create(ppf_plan_t* out, int N, int T, const float* h_host,
     if (bps == 0) return PPF_ERR_UNSUPPORTED;
     if (!is_pow2(N) || N < 4 || N > 4096 || T < 1 || T > 64) return PPF_ERR_UNSUPPORTED;
     if (in_dtype == PPF_IN_CI8 && N < 8) return PPF_ERR_UNSUPPORTED;
-    if (flags & ~(PPF_FLAG_FIR_ONLY | PPF_FLAG_GENERIC | 0xFF00u)) return PPF_ERR_INVALID_ARG;
+    if (flags & ~(PPF_FLAG_FIR_ONLY | PPF_FLAG_GENERIC | PPF_FLAG_OUT_F16 | 0xFF00u)) return PPF_ERR_INVALID_ARG;
+    if ((flags & PPF_FLAG_FIR_ONLY) && (flags & PPF_FLAG_OUT_F16)) return PPF_ERR_UNSUPPORTED;
     const int variant = (int)((flags >> 8) & 0xFFu) - 1;  // -1: tuned default
     if (variant >= 0 && variant >= ppf_variant_count(N, T, in_dtype)) return PPF_ERR_UNSUPPORTED;
 
@@ -215,13 +216,16 @@ ppf_status_t ppf_plan_create(ppf_plan_t* out, int N, int T, const float* h_host,
     v.tw = p->d_tw;
     v.sms = sms;
     v.err = d_err;
+    v.out_f16 = (flags & PPF_FLAG_OUT_F16) ? 1 : 0;
     p->view = v;
     p->fir_view = v;
     p->fir_view.fir_only = 1;
 
     p->fir_entry = ppf::generic_entry(N, (int)in_dtype);
-    p->entry = (flags & PPF_FLAG_GENERIC) ? p->fir_entry : ppf::select_fast_entry(N, T, (int)in_dtype, variant);
-    if (!p->entry.launch) p->entry = p->fir_entry;
+    const int out_f16 = (flags & PPF_FLAG_OUT_F16) ? 1 : 0;
+    const ppf::KernelEntry general = ppf::generic_entry(N, (int)in_dtype, out_f16);
+    p->entry = (flags & PPF_FLAG_GENERIC) ? general : ppf::select_fast_entry(N, T, (int)in_dtype, variant, out_f16);
+    if (!p->entry.launch) p->entry = general;
     if (!p->entry.launch || !p->fir_entry.launch) {
         free_plan_memory(p);
         delete p;
@@ -260,7 +264,7 @@ ppf_status_t ppf_execute(ppf_plan_t plan, const void* d_in, void* d_out, int64_t
     const PlanView& v = plan->view;
     if (!aligned16(d_in) || !aligned16(d_out)) return PPF_ERR_MISALIGNED;
     const size_t in_bytes = (size_t)(n_spectra + v.T - 1) * v.N * sample_bytes(plan->dtype);
-    const size_t out_bytes = (size_t)n_spectra * v.N * sizeof(float2);
+    const size_t out_bytes = (size_t)n_spectra * v.N * (v.out_f16 ? 4 : sizeof(float2));
     if (overlaps(d_in, in_bytes, d_out, out_bytes)) return PPF_ERR_MISALIGNED;
     if (pending_cuda_error()) return PPF_ERR_CUDA;
     if (*(volatile int*)plan->h_err) return PPF_ERR_TIMEOUT;
@@ -278,6 +282,7 @@ ppf_status_t ppf_execute_host(ppf_plan_t plan, const void* h_in, void* h_out, in
                               void* stream)
 {
     if (!plan || n_spectra < 0) return PPF_ERR_INVALID_ARG;
+    if (plan->view.out_f16) return PPF_ERR_UNSUPPORTED;
     if (n_spectra == 0) return PPF_OK;
     if (!h_in || !h_out) return PPF_ERR_INVALID_ARG;
     if (pending_cuda_error()) return PPF_ERR_CUDA;
@@ -340,6 +345,7 @@ ppf_status_t ppf_stream_open(ppf_plan_t plan, ppf_stream_t* out)
 {
     if (!plan || !out) return PPF_ERR_INVALID_ARG;
     *out = nullptr;
+    if (plan->view.out_f16) return PPF_ERR_UNSUPPORTED;
     ppf_stream_s* s = new (std::nothrow) ppf_stream_s();
     if (!s) return PPF_ERR_OUT_OF_MEMORY;
     s->plan = plan;

@@ -47,8 +47,10 @@ __host__ __device__ constexpr int stage2_stride(int N1, int K2)
     return s;
 }
 
-template <int N_, int T_, class In_, int P_, int N1_, int NT_, int RB_, int NCH_, int MINB_ = 1, int CPT_ = 2>
+template <int N_, int T_, class In_, int P_, int N1_, int NT_, int RB_, int NCH_, int MINB_ = 1, int CPT_ = 2,
+          class OT_ = float2>
 struct ClusterCfg {
+    using OT = OT_;  // output bin: float2 (complex64) or BinF16
     static constexpr int N = N_, T = T_, P = P_, N1 = N1_, NT = NT_, RB = RB_, NCH = NCH_, MINB = MINB_;
     // FIR channels per thread: 2 (a pair, one 2-sample load per row, scalar
     // FMAs) or 1 (one channel, coefficients duplicated as (h, h) so that one
@@ -214,7 +216,8 @@ __device__ __forceinline__ void stage1_upto_last(float2* A, const StageTwiddles<
 // runs of K2 consecutive bins.
 template <class C, int PP, class F>
 __device__ __forceinline__ void stage2_pass(float2* X, const StageTwiddles<C::N1, C::K2, C::NT>& tw,
-                                            float2* __restrict__ Yb, int rows, int rank, F&& after_last_read)
+                                            typename C::OT* __restrict__ Yb, int rows, int rank,
+                                            F&& after_last_read)
 {
     constexpr int L = C::N1, NT = C::NT, K2 = C::K2, RB = C::RB, RS1 = C::RS1;
     constexpr int R = fft_radix(L, PP), NS = fft_ns(L, PP);
@@ -258,9 +261,9 @@ __device__ __forceinline__ void stage2_pass(float2* X, const StageTwiddles<C::N1
 #pragma unroll
             for (int q = 0; q < R; ++q) x[pad_slot<NS, R>(base + q * NS)] = v[k][q];
         } else if (row < rows) {
-            float2* o = Yb + (int64_t)row * C::N + rank * K2 + k2l;
+            typename C::OT* o = Yb + (int64_t)row * C::N + rank * K2 + k2l;
 #pragma unroll
-            for (int q = 0; q < R; ++q) __stcs(o + (int64_t)C::N2 * (j + q * NS), v[k][q]);
+            for (int q = 0; q < R; ++q) st_bin(o + (int64_t)C::N2 * (j + q * NS), v[k][q]);
         }
     }
     if constexpr (!LAST) __syncthreads();
@@ -268,7 +271,7 @@ __device__ __forceinline__ void stage2_pass(float2* X, const StageTwiddles<C::N1
 
 template <class C, int PP = 0, class F>
 __device__ __forceinline__ void stage2(float2* X, const StageTwiddles<C::N1, C::K2, C::NT>& tw,
-                                       float2* __restrict__ Yb, int rows, int rank, F&& after_last_read)
+                                       typename C::OT* __restrict__ Yb, int rows, int rank, F&& after_last_read)
 {
     if constexpr (PP < fft_npass(C::N1)) {
         stage2_pass<C, PP>(X, tw, Yb, rows, rank, after_last_read);
@@ -351,7 +354,7 @@ ppf_cluster_kernel(const __grid_constant__ CUtensorMap xmap, const PpfWork wl, c
         }
         if (blo >= bhi) continue;
         const coef_t* __restrict__ h = static_cast<const coef_t*>(job.h);
-        float2* __restrict__ Y = job.Y;
+        typename C::OT* __restrict__ Y = reinterpret_cast<typename C::OT*>(job.Y);
         const int64_t S = job.S;
         const int nb = (int)(bhi - blo);
         const int64_t s_lo = blo * RB;

@@ -7,6 +7,7 @@
 
 #include <cstdio>
 #include <cstring>
+#include <type_traits>
 #include <mutex>
 
 #include "ppf_cluster.cuh"
@@ -132,8 +133,9 @@ template <class C>
 KernelEntry entry()
 {
     static char name[80];
-    std::snprintf(name, sizeof(name), "cluster:p%d:n1_%d:nt%d:rb%d:nch%d:b%d%s", C::P, C::N1, C::NT, C::RB, C::NCH,
-                  C::MINB, C::CPT == 1 ? ":c1" : "");
+    std::snprintf(name, sizeof(name), "cluster:p%d:n1_%d:nt%d:rb%d:nch%d:b%d%s%s", C::P, C::N1, C::NT, C::RB,
+                  C::NCH, C::MINB, C::CPT == 1 ? ":c1" : "",
+                  std::is_same<typename C::OT, BinF16>::value ? ":f16" : "");
     KernelEntry e;
     e.name = name;
     e.prepare = prepare_cluster<C>;
@@ -161,4 +163,12 @@ KernelEntry entry()
         if (idx == want && out)                                                                         \
             *out = cluster_detail::entry<ClusterCfg<NN, TT, In, P, N1, NT, RB, NCH, MINB, 1>>();        \
         ++idx;                                                                                          \
+    }
+// PPF_CVF(N, T, P, N1, NT, RB, NCH, MINB, channels per FIR thread): the
+// FP16-output twin of a tile shape.
+#define PPF_CVF(NN, TT, P, N1, NT, RB, NCH, MINB, CPT)                                                \
+    if (N == NN && T == TT) {                                                                         \
+        if (idx == want && out)                                                                       \
+            *out = cluster_detail::entry<ClusterCfg<NN, TT, In, P, N1, NT, RB, NCH, MINB, CPT, BinF16>>(); \
+        ++idx;                                                                                        \
     }

@@ -167,6 +167,21 @@ template <> struct Coef<InC32> { using type = float; };
 __device__ __forceinline__ float coef_f(float v) { return v; }
 __device__ __forceinline__ float coef_f(__half v) { return __half2float(v); }
 
+// ------------------------------------------------------------------ outputs
+// Output bins are complex64 (float2), or FP16 (I, Q) pairs rounded to nearest
+// (kept as their 32-bit pattern) for plans made with PPF_FLAG_OUT_F16.  The
+// kernels take the bin type as a template parameter; stores stream past the
+// caches (each output is written once).
+struct BinF16 {
+    uint32_t bits;
+};
+__device__ __forceinline__ void st_bin(float2* p, float2 v) { __stcs(p, v); }
+__device__ __forceinline__ void st_bin(BinF16* p, float2 v)
+{
+    const __half2 hv = __float22half2_rn(v);
+    __stcs(reinterpret_cast<unsigned*>(p), *reinterpret_cast<const unsigned*>(&hv));
+}
+
 // ------------------------------------------------------------------ work lists
 // One job of a launch: a contiguous input stream (S + T - 1 rows of N samples),
 // its S output spectra and its coefficients (each stream may have its own h).

@@ -26,9 +26,9 @@ __host__ __device__ constexpr int generic_smem_bytes(int N)
 
 // One Stockham pass over RB rows held in `buf` (in place).  The last pass
 // writes the spectra to global memory instead.
-template <int N, int RB, int NT, int P>
+template <int N, int RB, int NT, int P, class OT>
 __device__ __forceinline__ void fft_pass_block(float2* buf, const float2* __restrict__ tw,
-                                               float2* __restrict__ Yb, int rows)
+                                               OT* __restrict__ Yb, int rows)
 {
     constexpr int R = fft_radix(N, P);
     constexpr int NS = fft_ns(N, P);
@@ -54,9 +54,9 @@ __device__ __forceinline__ void fft_pass_block(float2* buf, const float2* __rest
             dft<R>(v[k]);
             if constexpr (LAST) {
                 if (row < rows) {
-                    float2* o = Yb + (int64_t)row * N + j;
+                    OT* o = Yb + (int64_t)row * N + j;
 #pragma unroll
-                    for (int q = 0; q < R; ++q) __stcs(o + q * NS, v[k][q]);
+                    for (int q = 0; q < R; ++q) st_bin(o + q * NS, v[k][q]);
                 }
             } else {
                 pass_store<N, R, NS>(buf, row, j, v[k]);
@@ -66,9 +66,9 @@ __device__ __forceinline__ void fft_pass_block(float2* buf, const float2* __rest
     if constexpr (!LAST) __syncthreads();
 }
 
-template <int N, int RB, int NT, int P = 0>
+template <int N, int RB, int NT, int P = 0, class OT>
 __device__ __forceinline__ void fft_block(float2* buf, const float2* __restrict__ tw,
-                                          float2* __restrict__ Yb, int rows)
+                                          OT* __restrict__ Yb, int rows)
 {
     if constexpr (P < fft_npass(N)) {
         fft_pass_block<N, RB, NT, P>(buf, tw, Yb, rows);
@@ -76,11 +76,11 @@ __device__ __forceinline__ void fft_block(float2* buf, const float2* __restrict_
     }
 }
 
-template <int N, class In, class Cf = typename Coef<In>::type>
+template <int N, class In, class Cf = typename Coef<In>::type, class OT = float2>
 __global__ void __launch_bounds__(kGenericThreads)
 ppf_generic_kernel(const typename In::raw* __restrict__ x,
                    const Cf* __restrict__ h,
-                   const float2* __restrict__ tw, float2* __restrict__ Y,
+                   const float2* __restrict__ tw, OT* __restrict__ Y,
                    int T, int64_t S, int fir_only)
 {
     constexpr int NT = kGenericThreads;
@@ -118,7 +118,7 @@ ppf_generic_kernel(const typename In::raw* __restrict__ x,
             }
             if (fir_only) {
                 if (row < rows) {
-                    float2* o = Y + (s0 + row) * (int64_t)N + c;
+                    float2* o = reinterpret_cast<float2*>(Y) + (s0 + row) * (int64_t)N + c;
                     o[0] = a0;
                     o[1] = a1;
                 }

@@ -16,6 +16,7 @@ struct PlanView {
     int sms = 0;                  // multiprocessors of the plan's device
     int grid_cap = 0;             // resident CTAs for the chosen kernel (set by prepare)
     int fir_only = 0;             // test hook: store y instead of Y
+    int out_f16 = 0;              // output bins are FP16 (I, Q) pairs instead of complex64
     int* err = nullptr;           // device-visible error word (mapped host memory)
     void* scratch = nullptr;      // plan-owned device scratch (split kernel: counters + exchange rows)
     size_t scratch_bytes = 0;     // set by prepare; the plan allocates it
@@ -40,8 +41,9 @@ struct KernelEntry {
     int cluster = 1;                     // CTAs per cluster
 };
 
-// General kernel for (N, dtype); runtime T.  Defined in ppf_generic.cu.
-KernelEntry generic_entry(int N, int dtype);
+// General kernel for (N, dtype), complex64 or (out_f16) FP16 output bins;
+// runtime T.  Defined in ppf_generic.cu.
+KernelEntry generic_entry(int N, int dtype, int out_f16 = 0);
 
 // Counts kernel launches issued by the library.
 void note_launch();

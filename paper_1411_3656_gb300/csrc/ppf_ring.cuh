@@ -23,8 +23,9 @@
 
 namespace ppf {
 
-template <int N_, int T_, class In_, int NT_, int RB_, int NCH_, int MINB_ = 1, int CPT_ = 2>
+template <int N_, int T_, class In_, int NT_, int RB_, int NCH_, int MINB_ = 1, int CPT_ = 2, class OT_ = float2>
 struct RingCfg {
+    using OT = OT_;  // output bin: float2 (complex64) or BinF16
     static constexpr int N = N_, T = T_, NT = NT_, RB = RB_, NCH = NCH_, MINB = MINB_;
     // FIR channels per thread: 2 (a pair, one 2-sample load per row, scalar
     // FMAs) or 1 (one channel, coefficients duplicated as (h, h) so that one
@@ -55,9 +56,9 @@ struct RingCfg {
 };
 
 // One Stockham pass from `in` to `out` (or to global memory for the last pass).
-template <int N, int RB, int NT, int P>
+template <int N, int RB, int NT, int P, class OT>
 __device__ __forceinline__ void fft_pass_pp(const float2* in, float2* out, const PassTwiddles<N, NT>& tw,
-                                            float2* __restrict__ Yb, int rows)
+                                            OT* __restrict__ Yb, int rows)
 {
     constexpr int R = fft_radix(N, P);
     constexpr int NS = fft_ns(N, P);
@@ -78,9 +79,9 @@ __device__ __forceinline__ void fft_pass_pp(const float2* in, float2* out, const
             dft<R>(v);
             if constexpr (LAST) {
                 if (row < rows) {
-                    float2* o = Yb + (int64_t)row * N + j;
+                    OT* o = Yb + (int64_t)row * N + j;
 #pragma unroll
-                    for (int q = 0; q < R; ++q) __stcs(o + q * NS, v[q]);
+                    for (int q = 0; q < R; ++q) st_bin(o + q * NS, v[q]);
                 }
             } else {
                 pass_store<N, R, NS>(out, row, j, v);
@@ -90,9 +91,9 @@ __device__ __forceinline__ void fft_pass_pp(const float2* in, float2* out, const
     if constexpr (!LAST) __syncthreads();
 }
 
-template <int N, int RB, int NT, int P = 0>
+template <int N, int RB, int NT, int P = 0, class OT>
 __device__ __forceinline__ void fft_rows_pp(float2* a, float2* b, const PassTwiddles<N, NT>& tw,
-                                            float2* __restrict__ Yb, int rows)
+                                            OT* __restrict__ Yb, int rows)
 {
     if constexpr (P < fft_npass(N)) {
         fft_pass_pp<N, RB, NT, P>(a, b, tw, Yb, rows);
@@ -153,7 +154,7 @@ ppf_ring_kernel(const PpfWork wl, const float2* __restrict__ tw, int* __restrict
         if (blo >= bhi) continue;
         const raw* __restrict__ x = static_cast<const raw*>(job.x);
         const coef_t* __restrict__ h = static_cast<const coef_t*>(job.h);
-        float2* __restrict__ Y = job.Y;
+        typename C::OT* __restrict__ Y = reinterpret_cast<typename C::OT*>(job.Y);
         const int64_t S = job.S;
         const int nb = (int)(bhi - blo);
         const int64_t s_lo = blo * RB;

@@ -2,6 +2,8 @@
 // per-N translation units (each TU instantiates the variants of one N).
 #pragma once
 
+#include <type_traits>
+
 #include <cstdio>
 
 #include "ppf_launch.h"
@@ -52,8 +54,8 @@ template <class C>
 KernelEntry entry()
 {
     static char name[64];
-    std::snprintf(name, sizeof(name), "ring:nt%d:rb%d:nch%d:b%d%s", C::NT, C::RB, C::NCH, C::MINB,
-                  C::CPT == 1 ? ":c1" : "");
+    std::snprintf(name, sizeof(name), "ring:nt%d:rb%d:nch%d:b%d%s%s", C::NT, C::RB, C::NCH, C::MINB,
+                  C::CPT == 1 ? ":c1" : "", std::is_same<typename C::OT, BinF16>::value ? ":f16" : "");
     KernelEntry e;
     e.name = name;
     e.prepare = prepare_ring<C>;
@@ -77,5 +79,13 @@ KernelEntry entry()
 #define PPF_RV1(NN, TT, NT, RB, NCH, MINB)                                                     \
     if (N == NN && T == TT) {                                                                  \
         if (idx == want && out) *out = ring_detail::entry<RingCfg<NN, TT, In, NT, RB, NCH, MINB, 1>>(); \
+        ++idx;                                                                                 \
+    }
+// PPF_RVF(N, T, threads, spectra per block, ring chunks, CTAs per SM, channels per
+// FIR thread): the FP16-output twin of a tile shape.
+#define PPF_RVF(NN, TT, NT, RB, NCH, MINB, CPT)                                                \
+    if (N == NN && T == TT) {                                                                  \
+        if (idx == want && out)                                                                \
+            *out = ring_detail::entry<RingCfg<NN, TT, In, NT, RB, NCH, MINB, CPT, BinF16>>();  \
         ++idx;                                                                                 \
     }

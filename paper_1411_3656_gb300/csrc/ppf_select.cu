@@ -6,6 +6,7 @@
 #include "ppf.h"
 #include "ppf_launch.h"
 
+#include <cstdio>
 #include <cstring>
 
 namespace ppf {
@@ -20,6 +21,8 @@ int split_variants_c32(int N, int T, int want, KernelEntry* out);
 int twopass_variants_c32(int N, int T, int want, KernelEntry* out);
 int twopass_variants_c16(int N, int T, int want, KernelEntry* out);
 int twopass_variants_ci8(int N, int T, int want, KernelEntry* out);
+int ring_variants_f16_c32(int N, int T, int want, KernelEntry* out);
+int cluster_variants_f16_c32(int N, int T, int want, KernelEntry* out);
 static int no_variants(int, int, int, KernelEntry*) { return 0; }
 
 using VariantFn = int (*)(int, int, int, KernelEntry*);
@@ -60,7 +63,26 @@ static int tuned_variant(int N, int T, int dtype)
     return 0;
 }
 
-KernelEntry select_fast_entry(int N, int T, int dtype, int variant)
+// FP16-output twin of a tile shape: the variant named "<name>:f16" (complex64
+// input only); an empty entry when none is compiled.
+static KernelEntry f16_twin(int N, int T, int dtype, const char* name)
+{
+    static const VariantFn lists[] = {ring_variants_f16_c32, cluster_variants_f16_c32};
+    if (dtype != 0 || !name) return KernelEntry{};
+    char want[112];
+    std::snprintf(want, sizeof(want), "%s:f16", name);
+    for (VariantFn f : lists) {
+        const int c = f(N, T, -1, nullptr);
+        for (int i = 0; i < c; ++i) {
+            KernelEntry e;
+            f(N, T, i, &e);
+            if (e.name && std::strcmp(e.name, want) == 0) return e;
+        }
+    }
+    return KernelEntry{};
+}
+
+KernelEntry select_fast_entry(int N, int T, int dtype, int variant, int out_f16)
 {
     KernelEntry e;
     const int n = variants(N, T, dtype, -1, nullptr);
@@ -68,7 +90,7 @@ KernelEntry select_fast_entry(int N, int T, int dtype, int variant)
     int v = variant >= 0 ? variant : tuned_variant(N, T, dtype);
     if (v >= n) v = 0;
     variants(N, T, dtype, v, &e);
-    return e;
+    return out_f16 ? f16_twin(N, T, dtype, e.name) : e;
 }
 
 }  // namespace ppf

@@ -34,11 +34,12 @@ def data_seconds(n_input_samples: int, samples_per_s: float = REALTIME_SAMPLES_P
     return n_input_samples / samples_per_s
 
 
-def algorithmic_bytes(N: int, T: int, S: int, dtype: str = "c32") -> int:
-    """Bytes one fused launch must move: input once, output once, coefficients once."""
+def algorithmic_bytes(N: int, T: int, S: int, dtype: str = "c32", out_bytes: int = 8) -> int:
+    """Bytes one fused launch must move: input once, output once (8 bytes per
+    complex64 bin, 4 for FP16 pairs), coefficients once."""
     if S <= 0:
         return 0
-    return (S + T - 1) * N * IN_BYTES[dtype] + S * N * 8 + N * T * COEF_BYTES[dtype]
+    return (S + T - 1) * N * IN_BYTES[dtype] + S * N * out_bytes + N * T * COEF_BYTES[dtype]
 
 
 def flops(N: int, T: int, S: int) -> float:

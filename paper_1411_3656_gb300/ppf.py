@@ -25,6 +25,7 @@ DTYPES = {"c32": 0, "c16": 1, "ci8": 2}
 SAMPLE_BYTES = {"c32": 8, "c16": 4, "ci8": 2}
 FLAG_FIR_ONLY = 1
 FLAG_GENERIC = 2
+FLAG_OUT_F16 = 4
 
 #: every entry point declared in include/ppf.h
 EXPORTS = ("ppf_plan_create", "ppf_plan_destroy", "ppf_execute", "ppf_execute_host",
@@ -270,8 +271,13 @@ class Plan:
     def n_spectra(self, x) -> int:
         return max(0, n_samples_of(x) // self.N - self.T + 1)
 
+    @property
+    def out_f16(self) -> bool:
+        return bool(self.flags & FLAG_OUT_F16)
+
     def execute(self, x, out=None, n_spectra: int | None = None, stream=None):
-        """Run the PPF on device tensor ``x``; returns complex64 [n_spectra, N]."""
+        """Run the PPF on device tensor ``x``; returns complex64 [n_spectra, N],
+        or float16 [n_spectra, N, 2] (I, Q) for a plan made with FLAG_OUT_F16."""
         import torch
         if dtype_of(x) != self.dtype:
             raise TypeError(f"plan expects {self.dtype} input, got {dtype_of(x)}")
@@ -280,7 +286,12 @@ class Plan:
         S = self.n_spectra(x) if n_spectra is None else int(n_spectra)
         if n_samples_of(x) < (S + self.T - 1) * self.N and S > 0:
             raise ValueError("input too short for n_spectra")
-        if out is None:
+        if self.out_f16:
+            if out is None:
+                out = torch.empty((S, self.N, 2), dtype=torch.float16, device=x.device)
+            elif out.numel() < 2 * S * self.N or out.dtype != torch.float16 or not out.is_contiguous():
+                raise ValueError("out must be a contiguous float16 tensor of at least n_spectra*N*2")
+        elif out is None:
             out = torch.empty((S, self.N), dtype=torch.complex64, device=x.device)
         elif out.numel() < S * self.N or out.dtype != torch.complex64 or not out.is_contiguous():
             raise ValueError("out must be a contiguous complex64 tensor of at least n_spectra*N")

@@ -95,3 +95,28 @@ def test_batch_argument_errors(ppf):
     assert lib.ppf_batch_execute(out.value, None) == 0
     assert lib.ppf_batch_destroy(out.value) == 0
     assert lib.ppf_batch_execute(None, None) == 1
+
+
+def test_batch_mixes_fp16_and_complex64_outputs(ppf):
+    """Jobs whose plans write FP16 bins (PPF_FLAG_OUT_F16) share launches with
+    complex64 jobs of the same kernel; each matches its own ppf_execute."""
+    import torch
+    specs = [(256, 8, 700), (256, 8, 310), (4096, 16, 41), (4096, 16, 12), (1024, 8, 333)]
+    jobs = []
+    for i, (N, T, S) in enumerate(specs):
+        g = np.random.default_rng(7000 + i)
+        h = g.standard_normal(N * T).astype(np.float32)
+        x = synth.stream(synth.samples_for(S, N, T), N, 7100 + i)
+        f16 = i % 2 == 0
+        plan = ppf.Plan(N, T, h, "c32", ppf.FLAG_OUT_F16 if f16 else 0)
+        xd = torch.from_numpy(x).cuda()
+        yd = (torch.full((S, N, 2), float("nan"), dtype=torch.float16, device="cuda") if f16
+              else torch.full((S, N), float("nan"), dtype=torch.complex64, device="cuda"))
+        jobs.append((plan, xd, yd, S))
+    batch = ppf.Batch(jobs)
+    batch.execute()
+    torch.cuda.synchronize()
+    for plan, xd, yd, S in jobs:
+        ref = plan(xd, n_spectra=S)
+        torch.cuda.synchronize()
+        assert torch.equal(yd, ref), (plan.kernel, plan.out_f16)

@@ -302,3 +302,51 @@ def test_full_size_sweep_cell_sampled(ppf, second_of_data, N, T):
     torch.cuda.empty_cache()
     ref = oracle.ppf_rows(x, h, N, T, rows)
     assert synth.rel_l2(got, ref) <= TOL32, kern
+
+
+@pytest.mark.parametrize("N,T", VARIANT_CELLS + [(64, 3), (1024, 13)])
+def test_fp16_output_every_variant(ppf, N, T):
+    """PPF_FLAG_OUT_F16: a plan runs the FP16-output twin of the tile shape its
+    complex64 counterpart runs (else the general kernel); its bins are that
+    shape's complex64 bins rounded to nearest (bitwise), hence within FP16
+    rounding (2^-11 relative per component; gate 1e-3 relative L2) of the oracle.
+    Checked for the tuned default, the general kernel and every forced variant."""
+    import torch
+    S = max(3, 40960 // N) + 3
+    x, h = _rand(N, T, S, 2200 + N + T)
+    ref = oracle.ppf(x, h, N, T, S)
+    xd = _dev(x)
+    flags = [0, ppf.FLAG_GENERIC] + [ppf.flag_variant(i) for i in range(ppf.ppf_variant_count(N, T, "c32"))]
+    twins = 0
+    for fl in flags:
+        p16 = ppf.Plan(N, T, h, "c32", fl | ppf.FLAG_OUT_F16)
+        p32 = ppf.Plan(N, T, h, "c32", fl)
+        if p16.kernel == "generic:f16":
+            p32 = ppf.Plan(N, T, h, "c32", ppf.FLAG_GENERIC)
+        else:
+            assert p16.kernel == p32.kernel + ":f16"
+            twins += 1
+        y32 = p32(xd, n_spectra=S)
+        y16 = p16(xd, n_spectra=S)
+        torch.cuda.synchronize()
+        assert y16.dtype == torch.float16 and tuple(y16.shape) == (S, N, 2)
+        assert torch.equal(y16, torch.view_as_real(y32).to(torch.float16)), p16.kernel
+        got = y16.float().cpu().numpy().view(np.complex64)[..., 0]
+        assert synth.rel_l2(got, ref) <= 1e-3, p16.kernel
+    if (N, T) in VARIANT_CELLS and N >= 256:
+        assert twins >= 1  # the tuned default of a sweep cell has an FP16 twin
+
+
+def test_fp16_output_unsupported_paths(ppf):
+    import torch
+    N, T = 256, 8
+    h = synth.hamming_sinc(N, T)
+    with pytest.raises(ppf.PPFError):
+        ppf.Plan(N, T, h, "c32", ppf.FLAG_OUT_F16 | ppf.FLAG_FIR_ONLY)
+    plan = ppf.Plan(N, T, h, "c32", ppf.FLAG_OUT_F16)
+    x = torch.zeros(16 * N, dtype=torch.complex64).pin_memory()
+    y = torch.zeros(16 * N, dtype=torch.complex64).pin_memory()
+    assert ppf.ppf_execute_host(plan.handle, x.data_ptr(), y.data_ptr(), 4, 0) == 2  # PPF_ERR_UNSUPPORTED
+    import ctypes
+    s = ctypes.c_void_p()
+    assert ppf.load().ppf_stream_open(plan.handle, ctypes.byref(s)) == 2
