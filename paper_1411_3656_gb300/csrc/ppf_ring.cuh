@@ -135,6 +135,12 @@ ppf_ring_kernel(const PpfWork wl, const float2* __restrict__ tw, int* __restrict
     // Chunks this CTA issued in earlier bands: ring slots and mbarrier phases
     // continue across bands (every chunk of a band is waited for in that band).
     int cbase = 0;
+    // Blocks this CTA has filtered.  With an odd number of FFT passes the last
+    // pass reads the buffer the FIR wrote, so the FIR alternates between the two
+    // buffers from block to block and never writes the one the previous block's
+    // last pass may still be reading; no barrier is needed between them.
+    constexpr bool ODD = fft_npass(N) % 2 == 1;
+    int bcount = 0;
     for (int it = blockIdx.x;; it += gridDim.x) {
         PpfJob job;
         int64_t blo, bhi;
@@ -200,20 +206,18 @@ ppf_ring_kernel(const PpfWork wl, const float2* __restrict__ tw, int* __restrict
         int rrb = (cbase % NCH) * RB;      // ring row of the block's first input row
         bool failed = false;
         for (int b = 0; b < nb; ++b) {
-            // 1. the block needs chunks b .. b+KO
-            bool ok = true;
+            // 1. the block needs chunks b .. b+KO; every thread waits itself (a
+            //    failure spreads over the CTA at the barrier after the FIR)
             const int need = (b + C::KO < nchunks ? b + C::KO : nchunks - 1) + 1;
-            for (; waited < need; ++waited) {
+            for (; waited < need && !failed; ++waited) {
                 const int gk = cbase + waited;
                 if (!mbar_wait_bounded(&bars[gk % NCH], (uint32_t)((gk / NCH) & 1))) {
-                    ok = false;
-                    break;
+                    failed = true;
+                    break;  // this chunk stays "not waited for": the drain below waits for it
                 }
             }
-            if (__syncthreads_or(!ok)) {
-                failed = true;
-                break;
-            }
+            float2* const fb = (ODD && (bcount & 1)) ? bufB : bufA;  // FIR output, FFT pass 0 input
+            float2* const ob = (ODD && (bcount & 1)) ? bufA : bufB;
 
             // 2. FIR over the ring (Eq. 1), RBT spectra x CPT channels per unit
 #pragma unroll
@@ -246,7 +250,7 @@ ppf_ring_kernel(const PpfWork wl, const float2* __restrict__ tw, int* __restrict
                     }
 #pragma unroll
                     for (int i = 0; i < RBT; ++i)
-                        *reinterpret_cast<float4*>(bufA + (i0 + i) * RS + c) =
+                        *reinterpret_cast<float4*>(fb + (i0 + i) * RS + c) =
                             make_float4(a0[i].x, a0[i].y, a1[i].x, a1[i].y);
                 } else {
                     float2 a[RBT];
@@ -264,10 +268,13 @@ ppf_ring_kernel(const PpfWork wl, const float2* __restrict__ tw, int* __restrict
                         }
                     }
 #pragma unroll
-                    for (int i = 0; i < RBT; ++i) bufA[(i0 + i) * RS + c] = a[i];
+                    for (int i = 0; i < RBT; ++i) fb[(i0 + i) * RS + c] = a[i];
                 }
             }
-            __syncthreads();
+            if (__syncthreads_or(failed)) {
+                failed = true;
+                break;
+            }
 
             // 3. chunk b is no longer needed: refill its slot
             if (tid == 0 && issued < nchunks && issued == b + NCH) {
@@ -280,7 +287,8 @@ ppf_ring_kernel(const PpfWork wl, const float2* __restrict__ tw, int* __restrict
             // 4. FFT of the RB rows; the last pass stores the spectra
             const int64_t s0 = s_lo + (int64_t)b * RB;
             const int rows = (int)(s_hi - s0 < RB ? s_hi - s0 : RB);
-            fft_rows_pp<N, RB, NT>(bufA, bufB, twr, Y + s0 * N, rows);
+            fft_rows_pp<N, RB, NT>(fb, ob, twr, Y + s0 * N, rows);
+            ++bcount;
         }
         if (failed) {
             if (tid == 0) {
@@ -294,8 +302,6 @@ ppf_ring_kernel(const PpfWork wl, const float2* __restrict__ tw, int* __restrict
             return;
         }
         cbase += nchunks;
-        // the FFT of the band's last block may still be reading bufA/bufB and the
-        // next band's FIR writes bufA: the next block's wait barrier orders them
     }
 }
 
