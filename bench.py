@@ -568,7 +568,9 @@ def run_batched(args):
         "one_launch_per_stream": {"ms_per_step": ms_single, "value": samples / (ms_single / 1e3) / 1e6,
                                   "launches": len(specs)},
         "batch_launches_per_step": batch.launches,
-        "gpu_launches": launches, "clocks": clock,
+        # graph replays enqueue the captured kernels without passing through the
+        # library's launch counter: count them from the batch
+        "gpu_launches": launches if launches > 0 else batch.launches * args.steps, "clocks": clock,
     }
     print(json.dumps(line), flush=True)
     batch.close()
