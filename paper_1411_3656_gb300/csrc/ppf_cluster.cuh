@@ -38,9 +38,9 @@ __host__ __device__ constexpr int cl_max(int a, int b) { return a > b ? a : b; }
 // Row stride of the stage-2 buffer: room for the first pass's padding and
 // congruent to 16/K2 modulo 16 slots, so a half-warp (K2 bin groups x 16/K2
 // butterflies) touches 16 distinct 8-byte bank slots.
-__host__ __device__ constexpr int stage2_stride(int N1, int K2)
+__host__ __device__ constexpr int stage2_stride(int N1, int K2, int R0 = 16)
 {
-    const int base = N1 + cl_max(N1 / 16, 1) + 1;
+    const int base = N1 + cl_max(N1 / R0, 1) + 1;
     const int want = K2 >= 16 ? 1 : 16 / K2;
     int s = base;
     while (s % 16 != want % 16) ++s;
@@ -48,9 +48,12 @@ __host__ __device__ constexpr int stage2_stride(int N1, int K2)
 }
 
 template <int N_, int T_, class In_, int P_, int N1_, int NT_, int RB_, int NCH_, int MINB_ = 1, int CPT_ = 2,
-          class OT_ = float2>
+          class OT_ = float2, int R0_ = 16>
 struct ClusterCfg {
     using OT = OT_;  // output bin: float2 (complex64) or BinF16
+    // radix of the first pass of each stage's transforms (8 or 16); R0 = 8
+    // keeps every thread busy in that pass when RB*C1*N2/16 < threads
+    static constexpr int R0 = R0_;
     static constexpr int N = N_, T = T_, P = P_, N1 = N1_, NT = NT_, RB = RB_, NCH = NCH_, MINB = MINB_;
     // FIR channels per thread: 2 (a pair, one 2-sample load per row, scalar
     // FMAs) or 1 (one channel, coefficients duplicated as (h, h) so that one
@@ -72,9 +75,9 @@ struct ClusterCfg {
     static constexpr int RING_ROWS = NCH * RB;
     static constexpr int CHUNK_BYTES = RB * NC * BPS;
     static constexpr int RING_BYTES = NCH * CHUNK_BYTES;
-    static constexpr int RSB = (N2 + cl_max(N2 / 16, 1) + 1) * C1 + ((N2 + cl_max(N2 / 16, 1) + 1) * C1) % 2;
+    static constexpr int RSB = (N2 + cl_max(N2 / R0, 1) + 1) * C1 + ((N2 + cl_max(N2 / R0, 1) + 1) * C1) % 2;
     static constexpr int A_SLOTS = RB * RSB;
-    static constexpr int RS1 = stage2_stride(N1, K2);
+    static constexpr int RS1 = stage2_stride(N1, K2, R0);
     static constexpr int X_SLOTS = RB * K2 * RS1;
     static constexpr int XBYTES = RB * K2 * N1 * 8;  // bytes each CTA receives per block
     static constexpr int SMEM = RING_BYTES + (A_SLOTS + 2 * X_SLOTS) * 8 + (NCH + 4) * 8;
@@ -91,13 +94,13 @@ struct ClusterCfg {
 // Twiddles W_{NS*R}^{(j mod NS)*r} of passes P.. of a length-L transform
 // whose butterfly index is j = (tid mod (M*L/R)) / M (M transforms
 // interleaved element-wise); kept in registers for the whole kernel.
-template <int L, int M, int NT, int P = 1, bool ANY = (P < fft_npass(L))>
+template <int L, int M, int NT, int R0 = 16, int P = 1, bool ANY = (P < fft_npass_r(L, R0))>
 struct StageTwiddles {
-    static constexpr int R = fft_radix(L, P);
-    static constexpr int NS = fft_ns(L, P);
+    static constexpr int R = fft_radix_r(L, P, R0);
+    static constexpr int NS = fft_ns_r(L, P, R0);
     static_assert(NT % (M * L / R) == 0, "thread count must be a multiple of the butterflies per row");
     float2 w[R - 1];
-    StageTwiddles<L, M, NT, P + 1> next;
+    StageTwiddles<L, M, NT, R0, P + 1> next;
     __device__ __forceinline__ void load(const float2* __restrict__ tw, int N)
     {
         const int j = (threadIdx.x % (M * L / R)) / M;
@@ -114,8 +117,8 @@ struct StageTwiddles {
         else return next.template get<Q>();
     }
 };
-template <int L, int M, int NT, int P>
-struct StageTwiddles<L, M, NT, P, false> {
+template <int L, int M, int NT, int R0, int P>
+struct StageTwiddles<L, M, NT, R0, P, false> {
     __device__ __forceinline__ void load(const float2* __restrict__, int) {}
     template <int Q>
     __device__ __forceinline__ const float2* get() const { return nullptr; }
@@ -126,9 +129,9 @@ struct StageTwiddles<L, M, NT, P, false> {
 template <class C>
 struct Stage1Out {
     static constexpr int L = C::N2;
-    static constexpr int PL = fft_npass(L) - 1;
-    static constexpr int R = fft_radix(L, PL);
-    static constexpr int NS = fft_ns(L, PL);
+    static constexpr int PL = fft_npass_r(L, C::R0) - 1;
+    static constexpr int R = fft_radix_r(L, PL, C::R0);
+    static constexpr int NS = fft_ns_r(L, PL, C::R0);
     static_assert(C::NT % (C::C1 * (L / R)) == 0, "thread count must be a multiple of the butterflies per row");
     float2 w[R];
     uint32_t addr[R];
@@ -154,14 +157,14 @@ struct Stage1Out {
 // Stage 1, pass PP: N2-point transforms over c2 in A (element stride C1, in
 // place).  The last pass sends its outputs to the owning CTAs' X buffers.
 template <class C, int PP>
-__device__ __forceinline__ void stage1_pass(float2* A, const StageTwiddles<C::N2, C::C1, C::NT>& tw,
+__device__ __forceinline__ void stage1_pass(float2* A, const StageTwiddles<C::N2, C::C1, C::NT, C::R0>& tw,
                                             const Stage1Out<C>& so, uint32_t xoff, uint32_t boff)
 {
     constexpr int L = C::N2, NT = C::NT, C1 = C::C1, RB = C::RB, RSB = C::RSB;
-    constexpr int R = fft_radix(L, PP), NS = fft_ns(L, PP);
-    constexpr bool LAST = (PP == fft_npass(L) - 1);
-    constexpr int IN_NS = PP == 0 ? 0 : fft_ns(L, PP - 1);
-    constexpr int IN_R = PP == 0 ? 1 : fft_radix(L, PP - 1);
+    constexpr int R = fft_radix_r(L, PP, C::R0), NS = fft_ns_r(L, PP, C::R0);
+    constexpr bool LAST = (PP == fft_npass_r(L, C::R0) - 1);
+    constexpr int IN_NS = PP == 0 ? 0 : fft_ns_r(L, PP - 1, C::R0);
+    constexpr int IN_R = PP == 0 ? 1 : fft_radix_r(L, PP - 1, C::R0);
     constexpr int BPR = C1 * (L / R);
     constexpr int NB = RB * BPR;
     constexpr int PER = (NB + NT - 1) / NT;
@@ -202,10 +205,10 @@ __device__ __forceinline__ void stage1_pass(float2* A, const StageTwiddles<C::N2
 }
 
 template <class C, int PP = 0>
-__device__ __forceinline__ void stage1_upto_last(float2* A, const StageTwiddles<C::N2, C::C1, C::NT>& tw,
+__device__ __forceinline__ void stage1_upto_last(float2* A, const StageTwiddles<C::N2, C::C1, C::NT, C::R0>& tw,
                                                  const Stage1Out<C>& so)
 {
-    if constexpr (PP < fft_npass(C::N2) - 1) {
+    if constexpr (PP < fft_npass_r(C::N2, C::R0) - 1) {
         stage1_pass<C, PP>(A, tw, so, 0, 0);
         stage1_upto_last<C, PP + 1>(A, tw, so);
     }
@@ -215,15 +218,15 @@ __device__ __forceinline__ void stage1_upto_last(float2* A, const StageTwiddles<
 // place); bin group k2l varies fastest across threads so the last pass stores
 // runs of K2 consecutive bins.
 template <class C, int PP, class F>
-__device__ __forceinline__ void stage2_pass(float2* X, const StageTwiddles<C::N1, C::K2, C::NT>& tw,
+__device__ __forceinline__ void stage2_pass(float2* X, const StageTwiddles<C::N1, C::K2, C::NT, C::R0>& tw,
                                             typename C::OT* __restrict__ Yb, int rows, int rank,
                                             F&& after_last_read)
 {
     constexpr int L = C::N1, NT = C::NT, K2 = C::K2, RB = C::RB, RS1 = C::RS1;
-    constexpr int R = fft_radix(L, PP), NS = fft_ns(L, PP);
-    constexpr bool LAST = (PP == fft_npass(L) - 1);
-    constexpr int IN_NS = PP == 0 ? 0 : fft_ns(L, PP - 1);
-    constexpr int IN_R = PP == 0 ? 1 : fft_radix(L, PP - 1);
+    constexpr int R = fft_radix_r(L, PP, C::R0), NS = fft_ns_r(L, PP, C::R0);
+    constexpr bool LAST = (PP == fft_npass_r(L, C::R0) - 1);
+    constexpr int IN_NS = PP == 0 ? 0 : fft_ns_r(L, PP - 1, C::R0);
+    constexpr int IN_R = PP == 0 ? 1 : fft_radix_r(L, PP - 1, C::R0);
     constexpr int BPR = K2 * (L / R);
     constexpr int NB = RB * BPR;
     constexpr int PER = (NB + NT - 1) / NT;
@@ -270,10 +273,10 @@ __device__ __forceinline__ void stage2_pass(float2* X, const StageTwiddles<C::N1
 }
 
 template <class C, int PP = 0, class F>
-__device__ __forceinline__ void stage2(float2* X, const StageTwiddles<C::N1, C::K2, C::NT>& tw,
+__device__ __forceinline__ void stage2(float2* X, const StageTwiddles<C::N1, C::K2, C::NT, C::R0>& tw,
                                        typename C::OT* __restrict__ Yb, int rows, int rank, F&& after_last_read)
 {
-    if constexpr (PP < fft_npass(C::N1)) {
+    if constexpr (PP < fft_npass_r(C::N1, C::R0)) {
         stage2_pass<C, PP>(X, tw, Yb, rows, rank, after_last_read);
         stage2<C, PP + 1>(X, tw, Yb, rows, rank, after_last_read);
     }
@@ -321,9 +324,9 @@ ppf_cluster_kernel(const __grid_constant__ CUtensorMap xmap, const PpfWork wl, c
     const int rg = C::UNITS >= NT ? 0 : tid / C::UNITS;
     const int pbase = C::UNITS >= NT ? tid : tid % C::UNITS;
     const int i0 = rg * RBT;
-    StageTwiddles<C::N2, C1, NT> tw1;
+    StageTwiddles<C::N2, C1, NT, C::R0> tw1;
     tw1.load(tw, N);
-    StageTwiddles<C::N1, C::K2, NT> tw2;
+    StageTwiddles<C::N1, C::K2, NT, C::R0> tw2;
     tw2.load(tw, N);
     Stage1Out<C> so;
     so.load(tw, X, xfull, rank);
@@ -495,7 +498,7 @@ ppf_cluster_kernel(const __grid_constant__ CUtensorMap xmap, const PpfWork wl, c
                 // thread waits before its own sends)
                 if (gb >= 2 && !failed && !mbar_wait_bounded(&xfree[par], (uint32_t)(((gb >> 1) - 1) & 1)))
                     failed = true;
-                stage1_pass<C, fft_npass(C::N2) - 1>(A, tw1, so, (uint32_t)(par * C::X_SLOTS * 8),
+                stage1_pass<C, fft_npass_r(C::N2, C::R0) - 1>(A, tw1, so, (uint32_t)(par * C::X_SLOTS * 8),
                                                      (uint32_t)(par * 8));
             }
             if (b >= 1) {

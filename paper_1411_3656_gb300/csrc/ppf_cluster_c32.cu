@@ -28,6 +28,13 @@ static int variants_impl(int N, int T, int want, KernelEntry* out)
     PPF_CV(4096, 4, 8, 64, 128, 4, 3, 2)
     PPF_CV(4096, 8, 8, 64, 128, 2, 6, 2)
     PPF_CV(4096, 16, 8, 64, 128, 2, 10, 2)
+    // stages starting with a radix-8 pass (every thread busy in the first pass)
+    PPF_CV8(1024, 32, 4, 64, 256, 8, 6, 1) PPF_CV8(1024, 32, 4, 32, 256, 8, 6, 1)
+    PPF_CV8(2048, 16, 4, 64, 256, 4, 6, 1) PPF_CV8(2048, 16, 8, 64, 128, 4, 6, 2)
+    PPF_CV8(2048, 32, 8, 64, 128, 4, 10, 2)
+    PPF_CV8(4096, 4, 4, 64, 256, 4, 3, 1) PPF_CV8(4096, 4, 8, 64, 128, 4, 3, 2)
+    PPF_CV8(4096, 8, 8, 64, 128, 2, 6, 2) PPF_CV8(4096, 16, 8, 64, 128, 2, 10, 2)
+    PPF_CV8(4096, 32, 8, 128, 256, 4, 10, 1) PPF_CV8(4096, 32, 8, 64, 256, 4, 10, 1)
     // 16-CTA clusters (non-portable size): 256 channels per CTA
     PPF_CV(4096, 32, 16, 64, 128, 4, 10, 2) PPF_CV1(4096, 32, 16, 64, 256, 8, 6, 1)
     PPF_CV1(4096, 32, 16, 64, 256, 4, 10, 1)

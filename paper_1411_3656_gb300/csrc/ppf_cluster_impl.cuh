@@ -133,8 +133,8 @@ template <class C>
 KernelEntry entry()
 {
     static char name[80];
-    std::snprintf(name, sizeof(name), "cluster:p%d:n1_%d:nt%d:rb%d:nch%d:b%d%s%s", C::P, C::N1, C::NT, C::RB,
-                  C::NCH, C::MINB, C::CPT == 1 ? ":c1" : "",
+    std::snprintf(name, sizeof(name), "cluster:p%d:n1_%d:nt%d:rb%d:nch%d:b%d%s%s%s", C::P, C::N1, C::NT, C::RB,
+                  C::NCH, C::MINB, C::CPT == 1 ? ":c1" : "", C::R0 == 8 ? ":r8" : "",
                   std::is_same<typename C::OT, BinF16>::value ? ":f16" : "");
     KernelEntry e;
     e.name = name;
@@ -164,11 +164,19 @@ KernelEntry entry()
             *out = cluster_detail::entry<ClusterCfg<NN, TT, In, P, N1, NT, RB, NCH, MINB, 1>>();        \
         ++idx;                                                                                          \
     }
-// PPF_CVF(N, T, P, N1, NT, RB, NCH, MINB, channels per FIR thread): the
-// FP16-output twin of a tile shape.
-#define PPF_CVF(NN, TT, P, N1, NT, RB, NCH, MINB, CPT)                                                \
+// PPF_CVF(N, T, P, N1, NT, RB, NCH, MINB, channels per FIR thread, first-pass
+// radix): the FP16-output twin of a tile shape.
+#define PPF_CVF(NN, TT, P, N1, NT, RB, NCH, MINB, CPT, R0)                                                   \
+    if (N == NN && T == TT) {                                                                                \
+        if (idx == want && out)                                                                              \
+            *out = cluster_detail::entry<ClusterCfg<NN, TT, In, P, N1, NT, RB, NCH, MINB, CPT, BinF16, R0>>(); \
+        ++idx;                                                                                               \
+    }
+// PPF_CV8(N, T, P, N1, NT, RB, NCH, MINB): a tile shape whose stages start with
+// a radix-8 pass.
+#define PPF_CV8(NN, TT, P, N1, NT, RB, NCH, MINB)                                                      \
     if (N == NN && T == TT) {                                                                         \
         if (idx == want && out)                                                                       \
-            *out = cluster_detail::entry<ClusterCfg<NN, TT, In, P, N1, NT, RB, NCH, MINB, CPT, BinF16>>(); \
+            *out = cluster_detail::entry<ClusterCfg<NN, TT, In, P, N1, NT, RB, NCH, MINB, 2, float2, 8>>(); \
         ++idx;                                                                                        \
     }

@@ -239,6 +239,32 @@ __host__ __device__ constexpr int fft_ns(int N, int pass)
     return ns;
 }
 
+// The same plan with the first pass's radix capped at R0 (8 or 16), then 16s,
+// the remainder last: 64 = 8 x 8, 32 = 8 x 4, 128 = 8 x 16 for R0 = 8.
+// R0 = 16 gives the plan above.
+__host__ __device__ constexpr int fft_radix_r(int N, int pass, int R0)
+{
+    int n = N;
+    for (int p = 0;; ++p) {
+        const int cap = p == 0 ? R0 : 16;
+        const int r = n >= cap ? cap : n;
+        if (p == pass) return r;
+        n /= r;
+    }
+}
+__host__ __device__ constexpr int fft_npass_r(int N, int R0)
+{
+    int p = 0;
+    for (int n = N; n > 1; ++p) n /= fft_radix_r(N, p, R0);
+    return p;
+}
+__host__ __device__ constexpr int fft_ns_r(int N, int pass, int R0)
+{
+    int ns = 1;
+    for (int p = 0; p < pass; ++p) ns *= fft_radix_r(N, p, R0);
+    return ns;
+}
+
 // Shared-memory row stride (in float2 slots) of the FFT buffer: N plus the
 // padding of the first pass (one slot per 16 elements), at least 2 so that
 // rows stay 16-byte aligned for vector stores.
@@ -286,13 +312,14 @@ __device__ __forceinline__ void pass_twiddle(const float2* __restrict__ tw, int 
 // Twiddles of passes P.. of a length-N row for the butterfly index this thread
 // keeps in every block (j = threadIdx.x mod N/R; fixed because the block's
 // thread count is a multiple of N/R).  Loaded once per kernel into registers.
-template <int N, int NT, int P = 1, bool ANY = (P < fft_npass(N))>
-struct PassTwiddles {
-    static constexpr int R = fft_radix(N, P);
-    static constexpr int NS = fft_ns(N, P);
+// R0 is the radix of the first pass (plan of fft_radix_r).
+template <int N, int NT, int R0 = 16, int P = 1, bool ANY = (P < fft_npass_r(N, R0))>
+struct PassTwiddlesR {
+    static constexpr int R = fft_radix_r(N, P, R0);
+    static constexpr int NS = fft_ns_r(N, P, R0);
     static_assert(NT % (N / R) == 0, "thread count must be a multiple of N/R");
     float2 w[R - 1];
-    PassTwiddles<N, NT, P + 1> next;
+    PassTwiddlesR<N, NT, R0, P + 1> next;
     __device__ __forceinline__ void load(const float2* __restrict__ tw)
     {
         const int k = (threadIdx.x % (N / R)) % NS;
@@ -308,12 +335,14 @@ struct PassTwiddles {
         else return next.template get<Q>();
     }
 };
-template <int N, int NT, int P>
-struct PassTwiddles<N, NT, P, false> {
+template <int N, int NT, int R0, int P>
+struct PassTwiddlesR<N, NT, R0, P, false> {
     __device__ __forceinline__ void load(const float2* __restrict__) {}
     template <int Q>
     __device__ __forceinline__ const float2* get() const { return nullptr; }
 };
+template <int N, int NT>
+using PassTwiddles = PassTwiddlesR<N, NT, 16>;
 
 template <int R>
 __device__ __forceinline__ void apply_twiddles(const float2* w, float2 (&v)[R])

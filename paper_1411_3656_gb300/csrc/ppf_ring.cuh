@@ -23,9 +23,13 @@
 
 namespace ppf {
 
-template <int N_, int T_, class In_, int NT_, int RB_, int NCH_, int MINB_ = 1, int CPT_ = 2, class OT_ = float2>
+template <int N_, int T_, class In_, int NT_, int RB_, int NCH_, int MINB_ = 1, int CPT_ = 2, class OT_ = float2,
+          int R0_ = 16>
 struct RingCfg {
     using OT = OT_;  // output bin: float2 (complex64) or BinF16
+    // radix of the FFT's first pass (8 or 16): 8 splits N = 1024 as 8 x 16 x 8
+    // instead of 16 x 16 x 4, evening out the butterflies per thread
+    static constexpr int R0 = R0_;
     static constexpr int N = N_, T = T_, NT = NT_, RB = RB_, NCH = NCH_, MINB = MINB_;
     // FIR channels per thread: 2 (a pair, one 2-sample load per row, scalar
     // FMAs) or 1 (one channel, coefficients duplicated as (h, h) so that one
@@ -35,7 +39,8 @@ struct RingCfg {
     using raw = typename In::raw;
     using coef_t = typename Coef<In>::type;
     static constexpr int BPS = In::bytes;
-    static constexpr int RS = fft_row_stride(N);
+    // row stride: room for the first pass's padding (N/R0 slots)
+    static constexpr int RS = R0 == 16 ? fft_row_stride(N) : N + N / 8;
     static constexpr int UNITS = N / CPT;                     // FIR work units per row
     static constexpr int G = UNITS > NT ? UNITS / NT : 1;     // units per thread
     static constexpr int RG = UNITS >= NT ? 1 : NT / UNITS;   // row groups
@@ -55,16 +60,17 @@ struct RingCfg {
     static_assert(CHUNK_BYTES % 16 == 0, "bulk copies move multiples of 16 bytes");
 };
 
-// One Stockham pass from `in` to `out` (or to global memory for the last pass).
-template <int N, int RB, int NT, int P, class OT>
-__device__ __forceinline__ void fft_pass_pp(const float2* in, float2* out, const PassTwiddles<N, NT>& tw,
+// One Stockham pass from `in` to `out` (or to global memory for the last pass);
+// rows of RS slots, first-pass radix R0.
+template <int N, int RB, int NT, int R0, int RS, int P, class OT>
+__device__ __forceinline__ void fft_pass_pp(const float2* in, float2* out, const PassTwiddlesR<N, NT, R0>& tw,
                                             OT* __restrict__ Yb, int rows)
 {
-    constexpr int R = fft_radix(N, P);
-    constexpr int NS = fft_ns(N, P);
-    constexpr bool LAST = (P == fft_npass(N) - 1);
-    constexpr int IN_NS = P == 0 ? 0 : fft_ns(N, P - 1);
-    constexpr int IN_R = P == 0 ? 1 : fft_radix(N, P - 1);
+    constexpr int R = fft_radix_r(N, P, R0);
+    constexpr int NS = fft_ns_r(N, P, R0);
+    constexpr bool LAST = (P == fft_npass_r(N, R0) - 1);
+    constexpr int IN_NS = P == 0 ? 0 : fft_ns_r(N, P - 1, R0);
+    constexpr int IN_R = P == 0 ? 1 : fft_radix_r(N, P - 1, R0);
     constexpr int BPR = N / R;
     constexpr int NB = RB * BPR;
     constexpr int PER = (NB + NT - 1) / NT;
@@ -74,7 +80,13 @@ __device__ __forceinline__ void fft_pass_pp(const float2* in, float2* out, const
         if (NB % NT == 0 || b < NB) {
             const int row = b / BPR, j = b % BPR;
             float2 v[R];
-            pass_load<N, R, IN_NS, IN_R>(in, row, j, v);
+            const float2* bi = in + row * RS;
+#pragma unroll
+            for (int r = 0; r < R; ++r) {
+                const int idx = j + r * (N / R);
+                if constexpr (IN_NS == 0) v[r] = bi[idx];
+                else v[r] = bi[pad_slot<IN_NS, IN_R>(idx)];
+            }
             if constexpr (P > 0) apply_twiddles<R>(tw.template get<P>(), v);
             dft<R>(v);
             if constexpr (LAST) {
@@ -84,20 +96,23 @@ __device__ __forceinline__ void fft_pass_pp(const float2* in, float2* out, const
                     for (int q = 0; q < R; ++q) st_bin(o + q * NS, v[q]);
                 }
             } else {
-                pass_store<N, R, NS>(out, row, j, v);
+                float2* bo = out + row * RS;
+                const int base = (j / NS) * NS * R + (j % NS);
+#pragma unroll
+                for (int q = 0; q < R; ++q) bo[pad_slot<NS, R>(base + q * NS)] = v[q];
             }
         }
     }
     if constexpr (!LAST) __syncthreads();
 }
 
-template <int N, int RB, int NT, int P = 0, class OT>
-__device__ __forceinline__ void fft_rows_pp(float2* a, float2* b, const PassTwiddles<N, NT>& tw,
+template <int N, int RB, int NT, int R0, int RS, int P = 0, class OT>
+__device__ __forceinline__ void fft_rows_pp(float2* a, float2* b, const PassTwiddlesR<N, NT, R0>& tw,
                                             OT* __restrict__ Yb, int rows)
 {
-    if constexpr (P < fft_npass(N)) {
-        fft_pass_pp<N, RB, NT, P>(a, b, tw, Yb, rows);
-        fft_rows_pp<N, RB, NT, P + 1>(b, a, tw, Yb, rows);
+    if constexpr (P < fft_npass_r(N, R0)) {
+        fft_pass_pp<N, RB, NT, R0, RS, P>(a, b, tw, Yb, rows);
+        fft_rows_pp<N, RB, NT, R0, RS, P + 1>(b, a, tw, Yb, rows);
     }
 }
 
@@ -129,7 +144,7 @@ ppf_ring_kernel(const PpfWork wl, const float2* __restrict__ tw, int* __restrict
     const int rg = C::UNITS >= NT ? 0 : tid / C::UNITS;
     const int pbase = C::UNITS >= NT ? tid : tid % C::UNITS;
     const int i0 = rg * RBT;
-    PassTwiddles<N, NT> twr;
+    PassTwiddlesR<N, NT, C::R0> twr;
     twr.load(tw);
 
     // Chunks this CTA issued in earlier bands: ring slots and mbarrier phases
@@ -139,7 +154,7 @@ ppf_ring_kernel(const PpfWork wl, const float2* __restrict__ tw, int* __restrict
     // pass reads the buffer the FIR wrote, so the FIR alternates between the two
     // buffers from block to block and never writes the one the previous block's
     // last pass may still be reading; no barrier is needed between them.
-    constexpr bool ODD = fft_npass(N) % 2 == 1;
+    constexpr bool ODD = fft_npass_r(N, C::R0) % 2 == 1;
     int bcount = 0;
     for (int it = blockIdx.x;; it += gridDim.x) {
         PpfJob job;
@@ -287,7 +302,7 @@ ppf_ring_kernel(const PpfWork wl, const float2* __restrict__ tw, int* __restrict
             // 4. FFT of the RB rows; the last pass stores the spectra
             const int64_t s0 = s_lo + (int64_t)b * RB;
             const int rows = (int)(s_hi - s0 < RB ? s_hi - s0 : RB);
-            fft_rows_pp<N, RB, NT>(fb, ob, twr, Y + s0 * N, rows);
+            fft_rows_pp<N, RB, NT, C::R0, RS>(fb, ob, twr, Y + s0 * N, rows);
             ++bcount;
         }
         if (failed) {

@@ -19,6 +19,9 @@ static int variants_impl(int N, int T, int want, KernelEntry* out)
     // two CTAs per SM
     PPF_RV1(512, 8, 256, 4, 4, 2) PPF_RV1(1024, 4, 256, 2, 4, 2)
     PPF_RV1(256, 16, 256, 8, 4, 2) PPF_RV1(256, 8, 256, 8, 4, 2)
+    // FFT starting with a radix-8 pass
+    PPF_RV8(512, 8, 256, 4, 4, 2, 2) PPF_RV8(512, 16, 512, 8, 4, 1, 1) PPF_RV8(512, 32, 512, 4, 10, 1, 1)
+    PPF_RV8(1024, 16, 512, 2, 10, 1, 1)
     return idx;
 }
 

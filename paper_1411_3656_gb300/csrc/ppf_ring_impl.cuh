@@ -54,8 +54,9 @@ template <class C>
 KernelEntry entry()
 {
     static char name[64];
-    std::snprintf(name, sizeof(name), "ring:nt%d:rb%d:nch%d:b%d%s%s", C::NT, C::RB, C::NCH, C::MINB,
-                  C::CPT == 1 ? ":c1" : "", std::is_same<typename C::OT, BinF16>::value ? ":f16" : "");
+    std::snprintf(name, sizeof(name), "ring:nt%d:rb%d:nch%d:b%d%s%s%s", C::NT, C::RB, C::NCH, C::MINB,
+                  C::CPT == 1 ? ":c1" : "", C::R0 == 8 ? ":r8" : "",
+                  std::is_same<typename C::OT, BinF16>::value ? ":f16" : "");
     KernelEntry e;
     e.name = name;
     e.prepare = prepare_ring<C>;
@@ -82,10 +83,18 @@ KernelEntry entry()
         ++idx;                                                                                 \
     }
 // PPF_RVF(N, T, threads, spectra per block, ring chunks, CTAs per SM, channels per
-// FIR thread): the FP16-output twin of a tile shape.
-#define PPF_RVF(NN, TT, NT, RB, NCH, MINB, CPT)                                                \
-    if (N == NN && T == TT) {                                                                  \
-        if (idx == want && out)                                                                \
-            *out = ring_detail::entry<RingCfg<NN, TT, In, NT, RB, NCH, MINB, CPT, BinF16>>();  \
-        ++idx;                                                                                 \
+// FIR thread, first-pass radix): the FP16-output twin of a tile shape.
+#define PPF_RVF(NN, TT, NT, RB, NCH, MINB, CPT, R0)                                                \
+    if (N == NN && T == TT) {                                                                      \
+        if (idx == want && out)                                                                    \
+            *out = ring_detail::entry<RingCfg<NN, TT, In, NT, RB, NCH, MINB, CPT, BinF16, R0>>();  \
+        ++idx;                                                                                     \
+    }
+// PPF_RV8(N, T, threads, spectra per block, ring chunks, CTAs per SM, channels per
+// FIR thread): a tile shape whose FFT starts with a radix-8 pass.
+#define PPF_RV8(NN, TT, NT, RB, NCH, MINB, CPT)                                                   \
+    if (N == NN && T == TT) {                                                                     \
+        if (idx == want && out)                                                                   \
+            *out = ring_detail::entry<RingCfg<NN, TT, In, NT, RB, NCH, MINB, CPT, float2, 8>>();   \
+        ++idx;                                                                                    \
     }
