@@ -35,6 +35,7 @@ static int variants_impl(int N, int T, int want, KernelEntry* out)
     PPF_CV8(4096, 4, 4, 64, 256, 4, 3, 1) PPF_CV8(4096, 4, 8, 64, 128, 4, 3, 2)
     PPF_CV8(4096, 8, 8, 64, 128, 2, 6, 2) PPF_CV8(4096, 16, 8, 64, 128, 2, 10, 2)
     PPF_CV8(4096, 32, 8, 128, 256, 4, 10, 1) PPF_CV8(4096, 32, 8, 64, 256, 4, 10, 1)
+    PPF_CV8(1024, 32, 4, 64, 128, 4, 10, 2)
     // 16-CTA clusters (non-portable size): 256 channels per CTA
     PPF_CV(4096, 32, 16, 64, 128, 4, 10, 2) PPF_CV1(4096, 32, 16, 64, 256, 8, 6, 1)
     PPF_CV1(4096, 32, 16, 64, 256, 4, 10, 1)
