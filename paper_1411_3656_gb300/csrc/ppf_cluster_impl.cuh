@@ -172,6 +172,14 @@ KernelEntry entry()
             *out = cluster_detail::entry<ClusterCfg<NN, TT, In, P, N1, NT, RB, NCH, MINB, CPT, BinF16, R0>>(); \
         ++idx;                                                                                               \
     }
+// PPF_CV81(N, T, P, N1, NT, RB, NCH, MINB): one channel per FIR thread and a
+// radix-8 first pass.
+#define PPF_CV81(NN, TT, P, N1, NT, RB, NCH, MINB)                                                     \
+    if (N == NN && T == TT) {                                                                         \
+        if (idx == want && out)                                                                       \
+            *out = cluster_detail::entry<ClusterCfg<NN, TT, In, P, N1, NT, RB, NCH, MINB, 1, float2, 8>>(); \
+        ++idx;                                                                                        \
+    }
 // PPF_CV8(N, T, P, N1, NT, RB, NCH, MINB): a tile shape whose stages start with
 // a radix-8 pass.
 #define PPF_CV8(NN, TT, P, N1, NT, RB, NCH, MINB)                                                      \

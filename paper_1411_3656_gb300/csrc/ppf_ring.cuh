@@ -13,8 +13,8 @@
 //      shared-memory read feeds up to RBT multiply-adds per channel);
 //   3. refill the ring slot the block no longer needs;
 //   4. FFT of the RB filtered rows with Stockham radix-16 passes ping-ponging
-//      between two shared buffers; the last pass stores the spectra to global
-//      memory (coalesced, streaming).
+//      between two shared buffers (or in place in one); the last pass stores
+//      the spectra to global memory (coalesced, streaming).
 // Filtered data never leaves the chip.
 #pragma once
 
@@ -24,7 +24,7 @@
 namespace ppf {
 
 template <int N_, int T_, class In_, int NT_, int RB_, int NCH_, int MINB_ = 1, int CPT_ = 2, class OT_ = float2,
-          int R0_ = 16>
+          int R0_ = 16, int NBUF_ = 2>
 struct RingCfg {
     using OT = OT_;  // output bin: float2 (complex64) or BinF16
     // radix of the FFT's first pass (8 or 16): 8 splits N = 1024 as 8 x 16 x 8
@@ -50,7 +50,11 @@ struct RingCfg {
     static constexpr int CHUNK_BYTES = RB * N * BPS;
     static constexpr int RING_BYTES = NCH * CHUNK_BYTES;
     static constexpr int BUF_SLOTS = RB * RS;
-    static constexpr int FFT_BYTES = 2 * BUF_SLOTS * 8;
+    // FFT buffers: 2 (the passes ping-pong, one barrier per pass) or 1 (every
+    // pass in place: loads, barrier, stores, barrier), which frees room for a
+    // deeper ring or more spectra per block
+    static constexpr int NBUF = NBUF_;
+    static constexpr int FFT_BYTES = NBUF * BUF_SLOTS * 8;
     static constexpr int SMEM = RING_BYTES + FFT_BYTES + NCH * 8;
     static_assert(N >= 64, "ring kernel handles N >= 64");
     static_assert(CPT == 1 || CPT == 2, "one channel or a pair per thread");
@@ -58,6 +62,8 @@ struct RingCfg {
     static_assert(RB % RG == 0 && RBT >= 1, "rows per block must split over row groups");
     static_assert(NCH >= KO + 2, "ring must hold a block's window plus one chunk in flight");
     static_assert(CHUNK_BYTES % 16 == 0, "bulk copies move multiples of 16 bytes");
+    static_assert(NBUF == 1 || NBUF == 2, "one or two FFT buffers");
+    static_assert(SMEM <= 232448, "shared memory per CTA");
 };
 
 // One Stockham pass from `in` to `out` (or to global memory for the last pass);
@@ -116,6 +122,73 @@ __device__ __forceinline__ void fft_rows_pp(float2* a, float2* b, const PassTwid
     }
 }
 
+// One Stockham pass in place (single FFT buffer): every thread first loads the
+// inputs of its butterflies, the CTA synchronises so that no element is
+// overwritten before every thread has read it, then the outputs go back to
+// the same rows (or, in the last pass, to global memory).  The barrier after
+// the last pass's loads also frees the buffer for the next block's FIR.
+template <int N, int RB, int NT, int R0, int RS, int P, class OT>
+__device__ __forceinline__ void fft_pass_ip(float2* buf, const PassTwiddlesR<N, NT, R0>& tw, OT* __restrict__ Yb,
+                                            int rows)
+{
+    constexpr int R = fft_radix_r(N, P, R0);
+    constexpr int NS = fft_ns_r(N, P, R0);
+    constexpr bool LAST = (P == fft_npass_r(N, R0) - 1);
+    constexpr int IN_NS = P == 0 ? 0 : fft_ns_r(N, P - 1, R0);
+    constexpr int IN_R = P == 0 ? 1 : fft_radix_r(N, P - 1, R0);
+    constexpr int BPR = N / R;
+    constexpr int NB = RB * BPR;
+    constexpr int PER = (NB + NT - 1) / NT;
+    float2 v[PER][R];
+#pragma unroll
+    for (int k = 0; k < PER; ++k) {
+        const int b = threadIdx.x + k * NT;
+        if (NB % NT == 0 || b < NB) {
+            const int row = b / BPR, j = b % BPR;
+            const float2* bi = buf + row * RS;
+#pragma unroll
+            for (int r = 0; r < R; ++r) {
+                const int idx = j + r * (N / R);
+                if constexpr (IN_NS == 0) v[k][r] = bi[idx];
+                else v[k][r] = bi[pad_slot<IN_NS, IN_R>(idx)];
+            }
+        }
+    }
+    __syncthreads();
+#pragma unroll
+    for (int k = 0; k < PER; ++k) {
+        const int b = threadIdx.x + k * NT;
+        if (NB % NT == 0 || b < NB) {
+            const int row = b / BPR, j = b % BPR;
+            if constexpr (P > 0) apply_twiddles<R>(tw.template get<P>(), v[k]);
+            dft<R>(v[k]);
+            if constexpr (LAST) {
+                if (row < rows) {
+                    OT* o = Yb + (int64_t)row * N + j;
+#pragma unroll
+                    for (int q = 0; q < R; ++q) st_bin(o + q * NS, v[k][q]);
+                }
+            } else {
+                float2* bo = buf + row * RS;
+                const int base = (j / NS) * NS * R + (j % NS);
+#pragma unroll
+                for (int q = 0; q < R; ++q) bo[pad_slot<NS, R>(base + q * NS)] = v[k][q];
+            }
+        }
+    }
+    if constexpr (!LAST) __syncthreads();
+}
+
+template <int N, int RB, int NT, int R0, int RS, int P = 0, class OT>
+__device__ __forceinline__ void fft_rows_ip(float2* buf, const PassTwiddlesR<N, NT, R0>& tw, OT* __restrict__ Yb,
+                                            int rows)
+{
+    if constexpr (P < fft_npass_r(N, R0)) {
+        fft_pass_ip<N, RB, NT, R0, RS, P>(buf, tw, Yb, rows);
+        fft_rows_ip<N, RB, NT, R0, RS, P + 1>(buf, tw, Yb, rows);
+    }
+}
+
 template <class C>
 __global__ void __launch_bounds__(C::NT, C::MINB)
 ppf_ring_kernel(const PpfWork wl, const float2* __restrict__ tw, int* __restrict__ err)
@@ -129,7 +202,7 @@ ppf_ring_kernel(const PpfWork wl, const float2* __restrict__ tw, int* __restrict
     extern __shared__ __align__(128) unsigned char smem[];
     unsigned char* ring = smem;
     float2* bufA = reinterpret_cast<float2*>(smem + C::RING_BYTES);
-    float2* bufB = bufA + C::BUF_SLOTS;
+    float2* bufB = C::NBUF == 2 ? bufA + C::BUF_SLOTS : bufA;
     uint64_t* bars = reinterpret_cast<uint64_t*>(smem + C::RING_BYTES + C::FFT_BYTES);
 
     const int tid = threadIdx.x;
@@ -150,11 +223,12 @@ ppf_ring_kernel(const PpfWork wl, const float2* __restrict__ tw, int* __restrict
     // Chunks this CTA issued in earlier bands: ring slots and mbarrier phases
     // continue across bands (every chunk of a band is waited for in that band).
     int cbase = 0;
-    // Blocks this CTA has filtered.  With an odd number of FFT passes the last
-    // pass reads the buffer the FIR wrote, so the FIR alternates between the two
-    // buffers from block to block and never writes the one the previous block's
-    // last pass may still be reading; no barrier is needed between them.
-    constexpr bool ODD = fft_npass_r(N, C::R0) % 2 == 1;
+    // Blocks this CTA has filtered.  With two buffers and an odd number of FFT
+    // passes the last pass reads the buffer the FIR wrote, so the FIR alternates
+    // between the two buffers from block to block and never writes the one the
+    // previous block's last pass may still be reading; no barrier is needed
+    // between them.
+    constexpr bool ODD = C::NBUF == 2 && fft_npass_r(N, C::R0) % 2 == 1;
     int bcount = 0;
     for (int it = blockIdx.x;; it += gridDim.x) {
         PpfJob job;
@@ -302,7 +376,8 @@ ppf_ring_kernel(const PpfWork wl, const float2* __restrict__ tw, int* __restrict
             // 4. FFT of the RB rows; the last pass stores the spectra
             const int64_t s0 = s_lo + (int64_t)b * RB;
             const int rows = (int)(s_hi - s0 < RB ? s_hi - s0 : RB);
-            fft_rows_pp<N, RB, NT, C::R0, RS>(fb, ob, twr, Y + s0 * N, rows);
+            if constexpr (C::NBUF == 2) fft_rows_pp<N, RB, NT, C::R0, RS>(fb, ob, twr, Y + s0 * N, rows);
+            else fft_rows_ip<N, RB, NT, C::R0, RS>(fb, twr, Y + s0 * N, rows);
             ++bcount;
         }
         if (failed) {

@@ -22,6 +22,10 @@ static int variants_impl(int N, int T, int want, KernelEntry* out)
     // FFT starting with a radix-8 pass
     PPF_RV8(512, 8, 256, 4, 4, 2, 2) PPF_RV8(512, 16, 512, 8, 4, 1, 1) PPF_RV8(512, 32, 512, 4, 10, 1, 1)
     PPF_RV8(1024, 16, 512, 2, 10, 1, 1)
+    // one FFT buffer: a ring long enough for 4096 x 4, or twice the spectra per block
+    PPF_RVS(4096, 4, 256, 1, 5, 1, 2) PPF_RVS(4096, 4, 256, 1, 6, 1, 2)
+    PPF_RVS(2048, 8, 256, 2, 6, 1, 2) PPF_RVS(1024, 16, 256, 4, 6, 1, 2) PPF_RVS(512, 32, 256, 8, 6, 1, 2)
+    PPF_RVS(256, 32, 256, 16, 5, 1, 1)
     return idx;
 }
 

@@ -54,8 +54,8 @@ template <class C>
 KernelEntry entry()
 {
     static char name[64];
-    std::snprintf(name, sizeof(name), "ring:nt%d:rb%d:nch%d:b%d%s%s%s", C::NT, C::RB, C::NCH, C::MINB,
-                  C::CPT == 1 ? ":c1" : "", C::R0 == 8 ? ":r8" : "",
+    std::snprintf(name, sizeof(name), "ring:nt%d:rb%d:nch%d:b%d%s%s%s%s", C::NT, C::RB, C::NCH, C::MINB,
+                  C::CPT == 1 ? ":c1" : "", C::R0 == 8 ? ":r8" : "", C::NBUF == 1 ? ":sb" : "",
                   std::is_same<typename C::OT, BinF16>::value ? ":f16" : "");
     KernelEntry e;
     e.name = name;
@@ -97,4 +97,19 @@ KernelEntry entry()
         if (idx == want && out)                                                                   \
             *out = ring_detail::entry<RingCfg<NN, TT, In, NT, RB, NCH, MINB, CPT, float2, 8>>();   \
         ++idx;                                                                                    \
+    }
+// PPF_RVS(N, T, threads, spectra per block, ring chunks, CTAs per SM, channels per
+// FIR thread): a tile shape with one FFT buffer (passes in place); PPF_RVFS is
+// its FP16-output twin.
+#define PPF_RVS(NN, TT, NT, RB, NCH, MINB, CPT)                                                       \
+    if (N == NN && T == TT) {                                                                         \
+        if (idx == want && out)                                                                       \
+            *out = ring_detail::entry<RingCfg<NN, TT, In, NT, RB, NCH, MINB, CPT, float2, 16, 1>>();   \
+        ++idx;                                                                                        \
+    }
+#define PPF_RVFS(NN, TT, NT, RB, NCH, MINB, CPT)                                                      \
+    if (N == NN && T == TT) {                                                                         \
+        if (idx == want && out)                                                                       \
+            *out = ring_detail::entry<RingCfg<NN, TT, In, NT, RB, NCH, MINB, CPT, BinF16, 16, 1>>();   \
+        ++idx;                                                                                        \
     }
