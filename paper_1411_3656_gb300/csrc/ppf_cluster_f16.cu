@@ -8,10 +8,7 @@ template <class In>
 static int variants_impl(int N, int T, int want, KernelEntry* out)
 {
     int idx = 0;
-    PPF_CVF(1024, 32, 4, 64, 128, 4, 10, 2, 2, 8)
-    PPF_CVF(2048, 16, 8, 64, 128, 4, 6, 2, 2, 8) PPF_CVF(2048, 32, 8, 64, 128, 4, 10, 2, 2, 8)
-    PPF_CVF(4096, 8, 8, 64, 128, 2, 6, 2, 2, 8)
-    PPF_CVF(4096, 16, 8, 64, 128, 2, 10, 2, 2, 8) PPF_CVF(4096, 32, 8, 128, 256, 4, 10, 1, 2, 8)
+    PPF_CVF(2048, 32, 8, 64, 128, 4, 10, 2, 2, 8)
     return idx;
 }
 

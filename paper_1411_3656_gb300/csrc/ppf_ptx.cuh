@@ -171,10 +171,50 @@ __device__ __forceinline__ void st_async_f2(uint32_t addr, float2 v, uint32_t rb
                  : "memory");
 }
 
+// The same for 16 bytes (16-byte aligned address).
+__device__ __forceinline__ void st_async_f4(uint32_t addr, float4 v, uint32_t rbar)
+{
+    asm volatile("st.async.shared::cluster.mbarrier::complete_tx::bytes.v4.f32 [%0], {%1, %2, %3, %4}, [%5];" ::"r"(
+                     addr),
+                 "f"(v.x), "f"(v.y), "f"(v.z), "f"(v.w), "r"(rbar)
+                 : "memory");
+}
+
 // Arrive once on an mbarrier of a peer CTA (cluster shared-memory address).
 __device__ __forceinline__ void mbar_arrive_remote(uint32_t rbar)
 {
     asm volatile("mbarrier.arrive.shared::cluster.b64 _, [%0];" ::"r"(rbar) : "memory");
+}
+
+// The same with release semantics at cluster scope: the shared-memory reads
+// this CTA made before (ordered by a CTA barrier) happen before anything a
+// peer does after observing the phase with mbar_wait_cluster_bounded.
+__device__ __forceinline__ void mbar_arrive_cluster(uint32_t rbar)
+{
+    asm volatile("mbarrier.arrive.release.cluster.shared::cluster.b64 _, [%0];" ::"r"(rbar) : "memory");
+}
+
+// Bounded wait with acquire semantics at cluster scope (pairs with mbar_arrive_cluster).
+__device__ __forceinline__ bool mbar_wait_cluster_bounded(uint64_t* bar, uint32_t parity,
+                                                          uint64_t limit_ns = kWaitLimitNs)
+{
+    auto try_wait = [&] {
+        uint32_t ok;
+        asm volatile(
+            "{\n\t.reg .pred p;\n\t"
+            "mbarrier.try_wait.parity.acquire.cluster.shared::cta.b64 p, [%1], %2;\n\t"
+            "selp.u32 %0, 1, 0, p;\n\t}"
+            : "=r"(ok)
+            : "r"(smem_u32(bar)), "r"(parity)
+            : "memory");
+        return ok != 0;
+    };
+    if (try_wait()) return true;
+    const uint64_t t0 = globaltimer_ns();
+    for (uint32_t i = 1;; ++i) {
+        if (try_wait()) return true;
+        if ((i & 63u) == 0 && globaltimer_ns() - t0 > limit_ns) return false;
+    }
 }
 
 }  // namespace ppf

@@ -126,10 +126,11 @@ __device__ __forceinline__ void fft_rows_pp(float2* a, float2* b, const PassTwid
 // inputs of its butterflies, the CTA synchronises so that no element is
 // overwritten before every thread has read it, then the outputs go back to
 // the same rows (or, in the last pass, to global memory).  The barrier after
-// the last pass's loads also frees the buffer for the next block's FIR.
-template <int N, int RB, int NT, int R0, int RS, int P, class OT>
+// the last pass's loads also frees the buffer for the next block's FIR; the
+// caller's `after_last_read` runs right after it.
+template <int N, int RB, int NT, int R0, int RS, int P, class OT, class F>
 __device__ __forceinline__ void fft_pass_ip(float2* buf, const PassTwiddlesR<N, NT, R0>& tw, OT* __restrict__ Yb,
-                                            int rows)
+                                            int rows, F&& after_last_read)
 {
     constexpr int R = fft_radix_r(N, P, R0);
     constexpr int NS = fft_ns_r(N, P, R0);
@@ -155,6 +156,7 @@ __device__ __forceinline__ void fft_pass_ip(float2* buf, const PassTwiddlesR<N, 
         }
     }
     __syncthreads();
+    if constexpr (LAST) after_last_read();
 #pragma unroll
     for (int k = 0; k < PER; ++k) {
         const int b = threadIdx.x + k * NT;
@@ -179,13 +181,13 @@ __device__ __forceinline__ void fft_pass_ip(float2* buf, const PassTwiddlesR<N, 
     if constexpr (!LAST) __syncthreads();
 }
 
-template <int N, int RB, int NT, int R0, int RS, int P = 0, class OT>
+template <int N, int RB, int NT, int R0, int RS, int P = 0, class OT, class F>
 __device__ __forceinline__ void fft_rows_ip(float2* buf, const PassTwiddlesR<N, NT, R0>& tw, OT* __restrict__ Yb,
-                                            int rows)
+                                            int rows, F&& after_last_read)
 {
     if constexpr (P < fft_npass_r(N, R0)) {
-        fft_pass_ip<N, RB, NT, R0, RS, P>(buf, tw, Yb, rows);
-        fft_rows_ip<N, RB, NT, R0, RS, P + 1>(buf, tw, Yb, rows);
+        fft_pass_ip<N, RB, NT, R0, RS, P>(buf, tw, Yb, rows, after_last_read);
+        fft_rows_ip<N, RB, NT, R0, RS, P + 1>(buf, tw, Yb, rows, after_last_read);
     }
 }
 
@@ -377,7 +379,7 @@ ppf_ring_kernel(const PpfWork wl, const float2* __restrict__ tw, int* __restrict
             const int64_t s0 = s_lo + (int64_t)b * RB;
             const int rows = (int)(s_hi - s0 < RB ? s_hi - s0 : RB);
             if constexpr (C::NBUF == 2) fft_rows_pp<N, RB, NT, C::R0, RS>(fb, ob, twr, Y + s0 * N, rows);
-            else fft_rows_ip<N, RB, NT, C::R0, RS>(fb, twr, Y + s0 * N, rows);
+            else fft_rows_ip<N, RB, NT, C::R0, RS>(fb, twr, Y + s0 * N, rows, [] {});
             ++bcount;
         }
         if (failed) {

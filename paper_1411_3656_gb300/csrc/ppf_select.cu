@@ -21,8 +21,10 @@ int split_variants_c32(int N, int T, int want, KernelEntry* out);
 int twopass_variants_c32(int N, int T, int want, KernelEntry* out);
 int twopass_variants_c16(int N, int T, int want, KernelEntry* out);
 int twopass_variants_ci8(int N, int T, int want, KernelEntry* out);
+int gather_variants_c32(int N, int T, int want, KernelEntry* out);
 int ring_variants_f16_c32(int N, int T, int want, KernelEntry* out);
 int cluster_variants_f16_c32(int N, int T, int want, KernelEntry* out);
+int gather_variants_f16_c32(int N, int T, int want, KernelEntry* out);
 static int no_variants(int, int, int, KernelEntry*) { return 0; }
 
 using VariantFn = int (*)(int, int, int, KernelEntry*);
@@ -30,10 +32,10 @@ using VariantFn = int (*)(int, int, int, KernelEntry*);
 // Number of variants for (N, T, dtype); fills *out with variant `want` if it exists.
 int variants(int N, int T, int dtype, int want, KernelEntry* out)
 {
-    static const VariantFn lists[3][4] = {
-        {ring_variants_c32, cluster_variants_c32, split_variants_c32, twopass_variants_c32},
-        {ring_variants_c16, cluster_variants_c16, no_variants, twopass_variants_c16},
-        {ring_variants_ci8, cluster_variants_ci8, no_variants, twopass_variants_ci8}};
+    static const VariantFn lists[3][5] = {
+        {ring_variants_c32, cluster_variants_c32, split_variants_c32, twopass_variants_c32, gather_variants_c32},
+        {ring_variants_c16, cluster_variants_c16, no_variants, twopass_variants_c16, no_variants},
+        {ring_variants_ci8, cluster_variants_ci8, no_variants, twopass_variants_ci8, no_variants}};
     if (dtype < 0 || dtype > 2) return 0;
     int n = 0;
     for (VariantFn f : lists[dtype]) {
@@ -67,7 +69,7 @@ static int tuned_variant(int N, int T, int dtype)
 // input only); an empty entry when none is compiled.
 static KernelEntry f16_twin(int N, int T, int dtype, const char* name)
 {
-    static const VariantFn lists[] = {ring_variants_f16_c32, cluster_variants_f16_c32};
+    static const VariantFn lists[] = {ring_variants_f16_c32, cluster_variants_f16_c32, gather_variants_f16_c32};
     if (dtype != 0 || !name) return KernelEntry{};
     char want[112];
     std::snprintf(want, sizeof(want), "%s:f16", name);
