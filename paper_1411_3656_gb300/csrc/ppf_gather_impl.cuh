@@ -79,8 +79,8 @@ template <class C>
 KernelEntry entry()
 {
     static char name[80];
-    std::snprintf(name, sizeof(name), "gather:p%d:nt%d:rb%d:nch%d%s", C::P, C::NT, C::RB, C::NCH,
-                  std::is_same<typename C::OT, BinF16>::value ? ":f16" : "");
+    std::snprintf(name, sizeof(name), "gather:p%d:nt%d:rb%d:nch%d:b%d%s%s", C::P, C::NT, C::RB, C::NCH, C::MINB,
+                  C::R0 == 8 ? ":r8" : "", std::is_same<typename C::OT, BinF16>::value ? ":f16" : "");
     KernelEntry e;
     e.name = name;
     e.prepare = prepare_gather<C>;
@@ -94,16 +94,16 @@ KernelEntry entry()
 }  // namespace gather_detail
 }  // namespace ppf
 
-// PPF_GV(N, T, cluster size, threads, spectra per CTA and round, ring chunks):
-// one gather-kernel variant; PPF_GVF is its FP16-output twin.
-#define PPF_GV(NN, TT, P, NT, RB, NCH)                                                              \
-    if (N == NN && T == TT) {                                                                       \
-        if (idx == want && out) *out = gather_detail::entry<GatherCfg<NN, TT, In, P, NT, RB, NCH>>(); \
-        ++idx;                                                                                      \
+// PPF_GV(N, T, cluster size, threads, spectra per CTA and round, ring chunks,
+// CTAs per SM): one gather-kernel variant; PPF_GVF is its FP16-output twin.
+#define PPF_GV(NN, TT, P, NT, RB, NCH, MINB)                                                              \
+    if (N == NN && T == TT) {                                                                             \
+        if (idx == want && out) *out = gather_detail::entry<GatherCfg<NN, TT, In, P, NT, RB, NCH, MINB>>(); \
+        ++idx;                                                                                            \
     }
-#define PPF_GVF(NN, TT, P, NT, RB, NCH)                                                             \
-    if (N == NN && T == TT) {                                                                       \
-        if (idx == want && out)                                                                     \
-            *out = gather_detail::entry<GatherCfg<NN, TT, In, P, NT, RB, NCH, BinF16>>();           \
-        ++idx;                                                                                      \
+#define PPF_GVF(NN, TT, P, NT, RB, NCH, MINB)                                                             \
+    if (N == NN && T == TT) {                                                                             \
+        if (idx == want && out)                                                                           \
+            *out = gather_detail::entry<GatherCfg<NN, TT, In, P, NT, RB, NCH, MINB, BinF16>>();           \
+        ++idx;                                                                                            \
     }

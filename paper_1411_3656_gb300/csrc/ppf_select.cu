@@ -22,6 +22,8 @@ int twopass_variants_c32(int N, int T, int want, KernelEntry* out);
 int twopass_variants_c16(int N, int T, int want, KernelEntry* out);
 int twopass_variants_ci8(int N, int T, int want, KernelEntry* out);
 int gather_variants_c32(int N, int T, int want, KernelEntry* out);
+int gather_variants_c16(int N, int T, int want, KernelEntry* out);
+int gather_variants_ci8(int N, int T, int want, KernelEntry* out);
 int ring_variants_f16_c32(int N, int T, int want, KernelEntry* out);
 int cluster_variants_f16_c32(int N, int T, int want, KernelEntry* out);
 int gather_variants_f16_c32(int N, int T, int want, KernelEntry* out);
@@ -34,8 +36,8 @@ int variants(int N, int T, int dtype, int want, KernelEntry* out)
 {
     static const VariantFn lists[3][5] = {
         {ring_variants_c32, cluster_variants_c32, split_variants_c32, twopass_variants_c32, gather_variants_c32},
-        {ring_variants_c16, cluster_variants_c16, no_variants, twopass_variants_c16, no_variants},
-        {ring_variants_ci8, cluster_variants_ci8, no_variants, twopass_variants_ci8, no_variants}};
+        {ring_variants_c16, cluster_variants_c16, no_variants, twopass_variants_c16, gather_variants_c16},
+        {ring_variants_ci8, cluster_variants_ci8, no_variants, twopass_variants_ci8, gather_variants_ci8}};
     if (dtype < 0 || dtype > 2) return 0;
     int n = 0;
     for (VariantFn f : lists[dtype]) {
