@@ -28,8 +28,7 @@
 
 namespace ppf {
 
-template <int N_, int T_, class In_, int P_, int NT_, int RB_, int NCH_, int MINB_ = 1, class OT_ = float2,
-          int R0_ = 16>
+template <int N_, int T_, class In_, int P_, int NT_, int RB_, int NCH_, int MINB_ = 1, class OT_ = float2>
 struct GatherCfg {
     using OT = OT_;  // output bin: float2 (complex64) or BinF16
     using In = In_;
@@ -37,7 +36,6 @@ struct GatherCfg {
     using coef_t = typename Coef<In>::type;
     static constexpr int N = N_, T = T_, P = P_, NT = NT_, RB = RB_, NCH = NCH_;
     static constexpr int MINB = MINB_;  // CTAs per SM the tile is built for
-    static constexpr int R0 = R0_;      // radix of the FFT's first pass (8 or 16)
     static constexpr int BPS = In::bytes;
     static constexpr int NC = N / P;                     // channels per CTA
     static constexpr int ROWS = P * RB;                  // spectra per round = input rows per ring chunk
@@ -50,7 +48,7 @@ struct GatherCfg {
     static constexpr int SEG_BYTES = NC * BPS;           // one input row's slice
     static constexpr int CHUNK_BYTES = ROWS * SEG_BYTES;
     static constexpr int RING_BYTES = NCH * CHUNK_BYTES;
-    static constexpr int RS = R0 == 16 ? fft_row_stride(N) : N + N / 8;
+    static constexpr int RS = fft_row_stride(N);
     static constexpr int X_SLOTS = RB * RS;              // the FFT buffer
     static constexpr int XBYTES = RB * N * 8;            // bytes the buffer receives per round
     static constexpr int SMEM = RING_BYTES + X_SLOTS * 8 + (NCH + 2) * 8;
@@ -101,7 +99,7 @@ ppf_gather_kernel(const PpfWork wl, const float2* __restrict__ tw, int* __restri
     const int rg = C::UNITS >= NT ? 0 : tid / C::UNITS;
     const int pbase = C::UNITS >= NT ? tid : tid % C::UNITS;
     const int i0 = rg * RBT;
-    PassTwiddlesR<N, NT, C::R0> twr;
+    PassTwiddlesR<N, NT, 16> twr;
     twr.load(tw);
     const uint32_t xbase = smem_u32(X), fullbase = smem_u32(xfull), freebase = smem_u32(xfree);
 
@@ -236,7 +234,7 @@ ppf_gather_kernel(const PpfWork wl, const float2* __restrict__ tw, int* __restri
             const int64_t s0 = s_lo + (int64_t)k * ROWS + rank * RB;
             const int64_t left = s_hi - s0;
             const int rows = (int)(left < 0 ? 0 : (left < RB ? left : RB));
-            fft_rows_ip<N, RB, NT, C::R0, C::RS>(X, twr, Y + (rows > 0 ? s0 : 0) * N, rows, [&] {
+            fft_rows_ip<N, RB, NT, 16, C::RS>(X, twr, Y + (rows > 0 ? s0 : 0) * N, rows, [&] {
                 // 4. every thread's last read of the buffer is done: free it on every CTA
                 if (tid < P) mbar_arrive_cluster(map_shared_rank(freebase, (uint32_t)tid));
             });

@@ -79,8 +79,8 @@ template <class C>
 KernelEntry entry()
 {
     static char name[80];
-    std::snprintf(name, sizeof(name), "gather:p%d:nt%d:rb%d:nch%d:b%d%s%s", C::P, C::NT, C::RB, C::NCH, C::MINB,
-                  C::R0 == 8 ? ":r8" : "", std::is_same<typename C::OT, BinF16>::value ? ":f16" : "");
+    std::snprintf(name, sizeof(name), "gather:p%d:nt%d:rb%d:nch%d:b%d%s", C::P, C::NT, C::RB, C::NCH, C::MINB,
+                  std::is_same<typename C::OT, BinF16>::value ? ":f16" : "");
     KernelEntry e;
     e.name = name;
     e.prepare = prepare_gather<C>;
