@@ -106,14 +106,15 @@ def kernel_source_hash() -> str:
     return hh.hexdigest()
 
 
-def measured_traffic(workload: str, dtype: str):
-    """DRAM bytes per step from the committed ncu summary, if it was taken on this kernel build."""
+def measured_traffic(workload: str, dtype: str, key: str = "traffic_bytes_per_step"):
+    """DRAM bytes from the committed ncu summary (per step, or per launch of one
+    cell with key "traffic_bytes_<N>x<T>"), if it was taken on this kernel build."""
     path = os.path.join(ROOT, "profiles", f"traffic_{workload}_{dtype}.txt")
     try:
         kv = dict(line.split(":", 1) for line in open(path) if ":" in line and not line.startswith("#"))
         if kv.get("source_sha256", "").strip() != kernel_source_hash():
             return None
-        return float(kv["traffic_bytes_per_step"])
+        return float(kv[key])
     except Exception:
         return None
 
@@ -413,6 +414,14 @@ def run_ours(args):
             "gflops": round(metrics.flops(N, T, S) / (ms / 1e3) / 1e9, 1)})
     achieved = tot_bytes / (tot_kernel_ms / 1e3) / 1e9
     data_s = sum(metrics.data_seconds((S + T - 1) * N) for N, T, S, _ in plans)
+    # the dominant launch: the cell with the longest average launch
+    dom = max(cell_rows, key=lambda c: c["ms"])
+    dom_bytes = metrics.algorithmic_bytes(dom["N"], dom["T"], dom["S"], dtype, out_bytes)
+    full_size = not args.cells and args.seconds == 1.0 and args.out_dtype == "c64"
+    dominant = {"cell": f'{dom["N"]}:{dom["T"]}', "kernel": dom["kernel"], "ms": dom["ms"],
+                "achieved": dom["GBs"], "frac": dom["frac_hbm"], "algorithmic_bytes": dom_bytes,
+                "traffic": measured_traffic(args.workload, dtype, f'traffic_bytes_{dom["N"]}x{dom["T"]}')
+                if full_size else None}
 
     # e2e through the public host-buffer entry point (pinned memory, copies inside)
     e2e = None
@@ -467,10 +476,10 @@ def run_ours(args):
             "x_realtime": data_s * args.steps / (elapsed_ms / 1e3),
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s",
                          "frac": achieved / hbm,
-                         "traffic": measured_traffic(args.workload, dtype)
-                         if (not args.cells and args.seconds == 1.0 and args.out_dtype == "c64") else None,
+                         "traffic": measured_traffic(args.workload, dtype) if full_size else None,
                          "algorithmic_bytes_per_step": tot_bytes,
-                         "kernel": "fused FIR+FFT (all cells, byte-weighted)", "peak_source": peak_src},
+                         "kernel": "fused FIR+FFT (all cells, byte-weighted)", "peak_source": peak_src,
+                         "dominant": dominant},
             "clocks": clock,
             "e2e": e2e,
             "gpu_launches": launches,
