@@ -282,6 +282,17 @@ __device__ __forceinline__ int pad_slot(int idx)
     else return idx + NS * (idx / (NS * R));
 }
 
+// Slots from element j to element j + L of a buffer written by a pass (NS, R),
+// for L a multiple of NS*R: the padding grows by L/R, so the R inputs of a
+// butterfly (j + r*L) sit at fixed offsets from pad_slot(j) and their
+// addresses need no per-element division.
+template <int NS, int R, int L>
+__host__ __device__ constexpr int pad_stride()
+{
+    static_assert(NS * R < 2 || L % (NS * R) == 0, "stride must span whole padding groups");
+    return (NS >= 16 || NS * R < 2) ? L : L + L / R;
+}
+
 // Load the R inputs of butterfly j of a pass from row `row` of `buf`.
 // InNS/InR describe the pass that wrote the buffer (InNS == 0: unpadded).
 template <int N, int R, int InNS, int InR>
@@ -289,11 +300,13 @@ __device__ __forceinline__ void pass_load(const float2* buf, int row, int j, flo
 {
     constexpr int RS = fft_row_stride(N);
     const float2* b = buf + row * RS;
+    if constexpr (InNS == 0) {
 #pragma unroll
-    for (int r = 0; r < R; ++r) {
-        const int idx = j + r * (N / R);
-        if constexpr (InNS == 0) v[r] = b[idx];
-        else v[r] = b[pad_slot<InNS, InR>(idx)];
+        for (int r = 0; r < R; ++r) v[r] = b[j + r * (N / R)];
+    } else {
+        const float2* bj = b + pad_slot<InNS, InR>(j);
+#pragma unroll
+        for (int r = 0; r < R; ++r) v[r] = bj[r * pad_stride<InNS, InR, N / R>()];
     }
 }
 
@@ -356,10 +369,10 @@ template <int N, int R, int NS>
 __device__ __forceinline__ void pass_store(float2* buf, int row, int j, const float2 (&v)[R])
 {
     constexpr int RS = fft_row_stride(N);
-    float2* b = buf + row * RS;
-    const int base = (j / NS) * NS * R + (j % NS);
+    // the R outputs lie in one padding group: one slot computation
+    float2* b = buf + row * RS + pad_slot<NS, R>((j / NS) * NS * R + (j % NS));
 #pragma unroll
-    for (int q = 0; q < R; ++q) b[pad_slot<NS, R>(base + q * NS)] = v[q];
+    for (int q = 0; q < R; ++q) b[q * NS] = v[q];
 }
 
 }  // namespace ppf

@@ -86,13 +86,9 @@ __device__ __forceinline__ void fft_pass_pp(const float2* in, float2* out, const
         if (NB % NT == 0 || b < NB) {
             const int row = b / BPR, j = b % BPR;
             float2 v[R];
-            const float2* bi = in + row * RS;
+            const float2* bi = in + row * RS + (IN_NS == 0 ? j : pad_slot<IN_NS, IN_R>(j));
 #pragma unroll
-            for (int r = 0; r < R; ++r) {
-                const int idx = j + r * (N / R);
-                if constexpr (IN_NS == 0) v[r] = bi[idx];
-                else v[r] = bi[pad_slot<IN_NS, IN_R>(idx)];
-            }
+            for (int r = 0; r < R; ++r) v[r] = bi[r * (IN_NS == 0 ? N / R : pad_stride<IN_NS, IN_R, N / R>())];
             if constexpr (P > 0) apply_twiddles<R>(tw.template get<P>(), v);
             dft<R>(v);
             if constexpr (LAST) {
@@ -102,10 +98,10 @@ __device__ __forceinline__ void fft_pass_pp(const float2* in, float2* out, const
                     for (int q = 0; q < R; ++q) st_bin(o + q * NS, v[q]);
                 }
             } else {
-                float2* bo = out + row * RS;
-                const int base = (j / NS) * NS * R + (j % NS);
+                // the R outputs lie in one padding group: one slot computation
+                float2* bo = out + row * RS + pad_slot<NS, R>((j / NS) * NS * R + (j % NS));
 #pragma unroll
-                for (int q = 0; q < R; ++q) bo[pad_slot<NS, R>(base + q * NS)] = v[q];
+                for (int q = 0; q < R; ++q) bo[q * NS] = v[q];
             }
         }
     }
@@ -146,13 +142,9 @@ __device__ __forceinline__ void fft_pass_ip(float2* buf, const PassTwiddlesR<N, 
         const int b = threadIdx.x + k * NT;
         if (NB % NT == 0 || b < NB) {
             const int row = b / BPR, j = b % BPR;
-            const float2* bi = buf + row * RS;
+            const float2* bi = buf + row * RS + (IN_NS == 0 ? j : pad_slot<IN_NS, IN_R>(j));
 #pragma unroll
-            for (int r = 0; r < R; ++r) {
-                const int idx = j + r * (N / R);
-                if constexpr (IN_NS == 0) v[k][r] = bi[idx];
-                else v[k][r] = bi[pad_slot<IN_NS, IN_R>(idx)];
-            }
+            for (int r = 0; r < R; ++r) v[k][r] = bi[r * (IN_NS == 0 ? N / R : pad_stride<IN_NS, IN_R, N / R>())];
         }
     }
     __syncthreads();
@@ -171,10 +163,9 @@ __device__ __forceinline__ void fft_pass_ip(float2* buf, const PassTwiddlesR<N, 
                     for (int q = 0; q < R; ++q) st_bin(o + q * NS, v[k][q]);
                 }
             } else {
-                float2* bo = buf + row * RS;
-                const int base = (j / NS) * NS * R + (j % NS);
+                float2* bo = buf + row * RS + pad_slot<NS, R>((j / NS) * NS * R + (j % NS));
 #pragma unroll
-                for (int q = 0; q < R; ++q) bo[pad_slot<NS, R>(base + q * NS)] = v[k][q];
+                for (int q = 0; q < R; ++q) bo[q * NS] = v[k][q];
             }
         }
     }
