@@ -446,7 +446,7 @@ ppf_cluster_kernel(const __grid_constant__ CUtensorMap xmap, const PpfWork wl, c
                             rr = rr >= RING_ROWS ? rr - RING_ROWS : rr;
                             const PV pv = *reinterpret_cast<const PV*>(ring + ((size_t)rr * NC + l) * BPS);
                             float2 v0, v1;
-                            Pair<typename C::In>::split(pv, v0, v1);
+                            split_cvt<typename C::In>(pv, v0, v1);
 #pragma unroll
                             for (int i = 0; i < RBT; ++i) {
                                 const int t = u - i;
@@ -471,7 +471,7 @@ ppf_cluster_kernel(const __grid_constant__ CUtensorMap xmap, const PpfWork wl, c
                         for (int u = 0; u < RBT + T - 1; ++u) {
                             int rr = rrb + i0 + u;
                             rr = rr >= RING_ROWS ? rr - RING_ROWS : rr;
-                            const float2 v = decode(*reinterpret_cast<const raw*>(ring + ((size_t)rr * NC + l) * BPS));
+                            const float2 v = decode_cvt(*reinterpret_cast<const raw*>(ring + ((size_t)rr * NC + l) * BPS));
 #pragma unroll
                             for (int i = 0; i < RBT; ++i) {
                                 const int t = u - i;

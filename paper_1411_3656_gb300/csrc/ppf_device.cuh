@@ -17,6 +17,7 @@
 
 #include <cuda_fp16.h>
 #include <cstdint>
+#include <type_traits>
 
 namespace ppf {
 
@@ -132,9 +133,27 @@ struct InC32 { using raw = float2;  static constexpr int bytes = 8; };
 struct InC16 { using raw = __half2; static constexpr int bytes = 4; };
 struct InCI8 { using raw = char2;   static constexpr int bytes = 2; };
 
+// int8 -> FP32 without a conversion instruction (conversions issue at a
+// quarter of the FP32 rate).  With the byte flipped to u = b + 128 and placed
+// under the exponent byte 0x4B, the word is the float 2^23 + u exactly (unit
+// spacing at 2^23); subtracting 2^23 + 128 leaves b exactly.  The result is
+// bitwise (float)b for every b; one byte permute per value and one packed
+// subtract per (I, Q) pair.  `flipped` is the packed bytes XOR 0x80 in each.
+__device__ __forceinline__ float2 s8x2_to_f32x2(uint32_t flipped, int k0)
+{
+    constexpr float kBias = 8388736.0f;  // 2^23 + 128
+    const float i = __uint_as_float(__byte_perm(flipped, 0x4B000000u, 0x7440u | k0));
+    const float q = __uint_as_float(__byte_perm(flipped, 0x4B000000u, 0x7440u | (k0 + 1)));
+    return csub(make_float2(i, q), make_float2(kBias, kBias));
+}
+
 __device__ __forceinline__ float2 decode(float2 v) { return v; }
 __device__ __forceinline__ float2 decode(__half2 v) { return __half22float2(v); }
-__device__ __forceinline__ float2 decode(char2 v) { return make_float2((float)v.x, (float)v.y); }
+__device__ __forceinline__ float2 decode(char2 v)
+{
+    const uint32_t w = (uint32_t)(uint8_t)v.x | ((uint32_t)(uint8_t)v.y << 8);
+    return s8x2_to_f32x2(w ^ 0x8080u, 0);
+}
 
 // Two consecutive samples as one vector: 16 B (c32), 8 B (c16), 4 B (ci8).
 template <class In> struct Pair;
@@ -156,10 +175,29 @@ template <> struct Pair<InCI8> {
     using vec = char4;
     __device__ static void split(const vec& p, float2& a, float2& b)
     {
-        a = make_float2((float)p.x, (float)p.y);
-        b = make_float2((float)p.z, (float)p.w);
+        const uint32_t w = *reinterpret_cast<const uint32_t*>(&p) ^ 0x80808080u;
+        a = s8x2_to_f32x2(w, 0);
+        b = s8x2_to_f32x2(w, 2);
     }
 };
+
+// The same decodes with int8 converted by the conversion instruction, which
+// runs on its own (quarter-rate) pipe: the better choice where the FP32 pipe
+// is the tighter resource (the four-step cluster kernel at large T measured
+// 10% slower with the byte-permute form).  Values are identical either way.
+template <class In>
+__device__ __forceinline__ void split_cvt(const typename Pair<In>::vec& p, float2& a, float2& b)
+{
+    if constexpr (std::is_same<In, InCI8>::value) {
+        a = make_float2((float)p.x, (float)p.y);
+        b = make_float2((float)p.z, (float)p.w);
+    } else {
+        Pair<In>::split(p, a, b);
+    }
+}
+__device__ __forceinline__ float2 decode_cvt(char2 v) { return make_float2((float)v.x, (float)v.y); }
+template <class R>
+__device__ __forceinline__ float2 decode_cvt(R v) { return decode(v); }
 
 // Coefficient storage: FP32 for complex64 input, FP16 for the reduced types.
 template <class In> struct Coef { using type = __half; };

@@ -1,0 +1,85 @@
+"""Reduced-precision storage at the plain workload's size, N=1024, T=8.
+
+The same N(0, 1) + tones stream (or, for int8, a seeded Gaussian of sigma 20
+rounded to ADC counts) goes through the fused PPF as complex64, as FP16 (I, Q)
+pairs and as int8 (I, Q) pairs; h is the Hamming-windowed sinc, stored FP16 on
+the device for the reduced types; FIR and FFT run in FP32.  Each result's
+relative L2 error is measured against the FP64 oracle three ways:
+
+  * on the stored input values with the caller's FP32 h (gated: 1e-5 for
+    complex64, 3e-3 for FP16 / int8, which covers the FP16 rounding of h);
+  * on the stored input values with the FP16-rounded h the device uses
+    (gated at 1e-5: the kernel's own FP32 arithmetic);
+  * on the input before it was rounded to FP16 / int8 (reported; gated only
+    loosely at twice the size the storage rounding alone predicts).
+
+Each case prints one ``precision:`` line with the three figures.
+"""
+import json
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_1411_3656_gb300 import synth
+
+pytestmark = pytest.mark.gpu
+
+N, T, S = 1024, 8, 1024
+SEED = synth.BASE_SEED + 3
+
+
+@pytest.fixture(scope="module")
+def ppf():
+    import torch
+    from paper_1411_3656_gb300 import build, ppf as mod
+    build.build()
+    mod.load()
+    assert torch.cuda.is_available()
+    return mod
+
+
+def _inputs(dtype):
+    """(stored input, the same samples before storage rounding as complex128)."""
+    n = synth.samples_for(S, N, T)
+    if dtype == "ci8":
+        g = synth.complex_gaussian(n, SEED, 20.0)
+        return synth.int8_iq(n, SEED), g.astype(np.complex128)
+    x = synth.stream(n, N, SEED)
+    if dtype == "c16":
+        return synth.to_fp16_iq(x), x.astype(np.complex128)
+    return x, x.astype(np.complex128)
+
+
+# relative error of rounding the samples themselves: FP16 keeps 11 significant
+# bits (unit roundoff 2^-11, ~2^-11/sqrt(3) rms relative per component for
+# values spread over a binade); int8 rounding of N(0, 20^2) adds uniform
+# noise of variance 1/12 per component against a variance of 400
+STORAGE_RMS = {"c32": 0.0, "c16": 2.0 ** -11 / np.sqrt(3.0), "ci8": np.sqrt(1.0 / 12.0) / 20.0}
+
+
+@pytest.mark.parametrize("dtype", ["c32", "c16", "ci8"])
+def test_precision_report_n1024_t8(ppf, dtype):
+    import torch
+    xs, x_orig = _inputs(dtype)
+    h = synth.hamming_sinc(N, T)
+    plan = ppf.Plan(N, T, h, dtype)
+    Y = plan(torch.from_numpy(np.ascontiguousarray(xs)).to("cuda"), n_spectra=S)
+    torch.cuda.synchronize()
+    Y = Y.cpu().numpy()
+    assert Y.shape == (S, N)
+
+    err_stored = synth.rel_l2(Y, oracle.ppf(xs, h, N, T, S))
+    h_dev = h if dtype == "c32" else h.astype(np.float16).astype(np.float32)
+    err_device_h = synth.rel_l2(Y, oracle.ppf(xs, h_dev, N, T, S))
+    err_unrounded = synth.rel_l2(Y, oracle.ppf(x_orig, h, N, T, S))
+    print("precision: " + json.dumps({
+        "N": N, "T": T, "S": S, "input": dtype, "kernel": plan.kernel,
+        "rel_l2_vs_oracle_on_stored_input": err_stored,
+        "rel_l2_vs_oracle_with_device_h": err_device_h,
+        "rel_l2_vs_oracle_on_unrounded_input": err_unrounded}))
+    plan.close()
+
+    assert err_device_h <= 1e-5, err_device_h
+    assert err_stored <= (1e-5 if dtype == "c32" else 3e-3), err_stored
+    assert err_unrounded <= max(1e-5, 2.0 * STORAGE_RMS[dtype] + 3e-3 * (dtype != "c32")), err_unrounded
