@@ -199,6 +199,25 @@ __device__ __forceinline__ float2 decode_cvt(char2 v) { return make_float2((floa
 template <class R>
 __device__ __forceinline__ float2 decode_cvt(R v) { return decode(v); }
 
+// One FIR tap of a channel pair stored as FP16: h = (h0, h1) and the samples
+// x = ((re0, im0), (re1, im1)) as FP16 pairs; a0 += h0 * x0, a1 += h1 * x1 per
+// component with the mixed-precision FMA (FP16 operands, FP32 accumulator:
+// the product of two FP16 values is exact in FP32 and the sum is rounded
+// once), the value fmaf((float)h, (float)x, acc) gives, with no conversions.
+__device__ __forceinline__ void fma_f16_pair(uint32_t hh, uint2 x, float2& a0, float2& a1)
+{
+    asm("{\n\t.reg .f16 h0, h1, r0, i0, r1, i1;\n\t"
+        "mov.b32 {h0, h1}, %4;\n\t"
+        "mov.b32 {r0, i0}, %5;\n\t"
+        "mov.b32 {r1, i1}, %6;\n\t"
+        "fma.rn.f32.f16 %0, h0, r0, %0;\n\t"
+        "fma.rn.f32.f16 %1, h0, i0, %1;\n\t"
+        "fma.rn.f32.f16 %2, h1, r1, %2;\n\t"
+        "fma.rn.f32.f16 %3, h1, i1, %3;\n\t}"
+        : "+f"(a0.x), "+f"(a0.y), "+f"(a1.x), "+f"(a1.y)
+        : "r"(hh), "r"(x.x), "r"(x.y));
+}
+
 // Coefficient storage: FP32 for complex64 input, FP16 for the reduced types.
 template <class In> struct Coef { using type = __half; };
 template <> struct Coef<InC32> { using type = float; };

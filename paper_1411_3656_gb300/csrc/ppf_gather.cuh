@@ -22,6 +22,8 @@
 // across CTAs, so there is no twiddle stage and no second exchange.
 #pragma once
 
+#include <type_traits>
+
 #include "ppf_device.cuh"
 #include "ppf_ptx.cuh"
 #include "ppf_ring.cuh"
@@ -152,14 +154,22 @@ ppf_gather_kernel(const PpfWork wl, const float2* __restrict__ tw, int* __restri
         }
 
         // coefficients of the owned channel pairs, in registers for the whole item
-        float hr[G][T][2];
+        // (FP16 input keeps each tap's coefficients as one FP16 pair and
+        // multiplies FP16 samples directly: fma_f16_pair)
+        constexpr bool MIX = std::is_same<typename C::In, InC16>::value;
+        float hr[MIX ? 1 : G][MIX ? 1 : T][2];
+        uint32_t hq[MIX ? G : 1][MIX ? T : 1];
 #pragma unroll
         for (int g = 0; g < G; ++g) {
             const int c = rank * NC + 2 * (pbase + g * NT);
 #pragma unroll
             for (int t = 0; t < T; ++t) {
-                hr[g][t][0] = coef_f(h[t * N + c]);
-                hr[g][t][1] = coef_f(h[t * N + c + 1]);
+                if constexpr (MIX) {
+                    hq[g][t] = *reinterpret_cast<const uint32_t*>(h + t * N + c);
+                } else {
+                    hr[g][t][0] = coef_f(h[t * N + c]);
+                    hr[g][t][1] = coef_f(h[t * N + c + 1]);
+                }
             }
         }
 
@@ -196,16 +206,24 @@ ppf_gather_kernel(const PpfWork wl, const float2* __restrict__ tw, int* __restri
                     int rr = rrb + i0 + u;
                     rr = rr >= RING_ROWS ? rr - RING_ROWS : rr;
                     const PV pv = *reinterpret_cast<const PV*>(ring + ((size_t)rr * NC + cl) * BPS);
-                    float2 v0, v1;
-                    Pair<typename C::In>::split(pv, v0, v1);
+                    if constexpr (MIX) {
 #pragma unroll
-                    for (int i = 0; i < RBT; ++i) {
-                        const int t = u - i;
-                        if (t >= 0 && t < T) {
-                            a0[i].x = fmaf(hr[g][t][0], v0.x, a0[i].x);
-                            a0[i].y = fmaf(hr[g][t][0], v0.y, a0[i].y);
-                            a1[i].x = fmaf(hr[g][t][1], v1.x, a1[i].x);
-                            a1[i].y = fmaf(hr[g][t][1], v1.y, a1[i].y);
+                        for (int i = 0; i < RBT; ++i) {
+                            const int t = u - i;
+                            if (t >= 0 && t < T) fma_f16_pair(hq[g][t], pv, a0[i], a1[i]);
+                        }
+                    } else {
+                        float2 v0, v1;
+                        Pair<typename C::In>::split(pv, v0, v1);
+#pragma unroll
+                        for (int i = 0; i < RBT; ++i) {
+                            const int t = u - i;
+                            if (t >= 0 && t < T) {
+                                a0[i].x = fmaf(hr[g][t][0], v0.x, a0[i].x);
+                                a0[i].y = fmaf(hr[g][t][0], v0.y, a0[i].y);
+                                a1[i].x = fmaf(hr[g][t][1], v1.x, a1[i].x);
+                                a1[i].y = fmaf(hr[g][t][1], v1.y, a1[i].y);
+                            }
                         }
                     }
                 }

@@ -18,6 +18,8 @@
 // Filtered data never leaves the chip.
 #pragma once
 
+#include <type_traits>
+
 #include "ppf_device.cuh"
 #include "ppf_ptx.cuh"
 
@@ -267,14 +269,20 @@ ppf_ring_kernel(const PpfWork wl, const float2* __restrict__ tw, int* __restrict
 
         // coefficients of this thread's channels, in FP32 registers (CPT = 1
         // keeps each as the pair (h, h))
-        float hr[C::CPT == 2 ? G : 1][C::CPT == 2 ? T : 1][2];
+        // FP16 input with channel pairs keeps each tap's coefficients as one
+        // FP16 pair and multiplies FP16 samples directly (fma_f16_pair)
+        constexpr bool MIX = C::CPT == 2 && std::is_same<typename C::In, InC16>::value;
+        float hr[C::CPT == 2 && !MIX ? G : 1][C::CPT == 2 && !MIX ? T : 1][2];
+        uint32_t hq[MIX ? G : 1][MIX ? T : 1];
         float2 hh[C::CPT == 1 ? G : 1][C::CPT == 1 ? T : 1];
 #pragma unroll
         for (int g = 0; g < G; ++g) {
             const int c = C::CPT * (pbase + g * NT);
 #pragma unroll
             for (int t = 0; t < T; ++t) {
-                if constexpr (C::CPT == 2) {
+                if constexpr (MIX) {
+                    hq[g][t] = *reinterpret_cast<const uint32_t*>(h + t * N + c);
+                } else if constexpr (C::CPT == 2) {
                     hr[g][t][0] = coef_f(h[t * N + c]);
                     hr[g][t][1] = coef_f(h[t * N + c + 1]);
                 } else {
@@ -317,16 +325,24 @@ ppf_ring_kernel(const PpfWork wl, const float2* __restrict__ tw, int* __restrict
                         int rr = rrb + i0 + u;
                         rr = rr >= RING_ROWS ? rr - RING_ROWS : rr;
                         const PV pv = *reinterpret_cast<const PV*>(ring + ((size_t)rr * N + c) * BPS);
-                        float2 v0, v1;
-                        Pair<typename C::In>::split(pv, v0, v1);
+                        if constexpr (MIX) {
 #pragma unroll
-                        for (int i = 0; i < RBT; ++i) {
-                            const int t = u - i;
-                            if (t >= 0 && t < T) {
-                                a0[i].x = fmaf(hr[g][t][0], v0.x, a0[i].x);
-                                a0[i].y = fmaf(hr[g][t][0], v0.y, a0[i].y);
-                                a1[i].x = fmaf(hr[g][t][1], v1.x, a1[i].x);
-                                a1[i].y = fmaf(hr[g][t][1], v1.y, a1[i].y);
+                            for (int i = 0; i < RBT; ++i) {
+                                const int t = u - i;
+                                if (t >= 0 && t < T) fma_f16_pair(hq[g][t], pv, a0[i], a1[i]);
+                            }
+                        } else {
+                            float2 v0, v1;
+                            Pair<typename C::In>::split(pv, v0, v1);
+#pragma unroll
+                            for (int i = 0; i < RBT; ++i) {
+                                const int t = u - i;
+                                if (t >= 0 && t < T) {
+                                    a0[i].x = fmaf(hr[g][t][0], v0.x, a0[i].x);
+                                    a0[i].y = fmaf(hr[g][t][0], v0.y, a0[i].y);
+                                    a1[i].x = fmaf(hr[g][t][1], v1.x, a1[i].x);
+                                    a1[i].y = fmaf(hr[g][t][1], v1.y, a1[i].y);
+                                }
                             }
                         }
                     }
