@@ -218,6 +218,20 @@ __device__ __forceinline__ void fma_f16_pair(uint32_t hh, uint2 x, float2& a0, f
         : "r"(hh), "r"(x.x), "r"(x.y));
 }
 
+// Two stored samples as FP16 (I, Q) pairs for fma_f16_pair: FP16 storage as
+// is; int8 exactly (with the byte flipped to u = b + 128 under the exponent
+// byte 0x64 the FP16 word is 1024 + u, and subtracting 1152 leaves b).
+__device__ __forceinline__ uint2 f16_pairs(uint2 p) { return p; }
+__device__ __forceinline__ uint2 f16_pairs(char4 p)
+{
+    const uint32_t f = *reinterpret_cast<const uint32_t*>(&p) ^ 0x80808080u;
+    const uint32_t w0 = __byte_perm(f, 0x64646464u, 0x4140u), w1 = __byte_perm(f, 0x64646464u, 0x4342u);
+    uint2 r;
+    asm("sub.rn.f16x2 %0, %1, %2;" : "=r"(r.x) : "r"(w0), "r"(0x64806480u));
+    asm("sub.rn.f16x2 %0, %1, %2;" : "=r"(r.y) : "r"(w1), "r"(0x64806480u));
+    return r;
+}
+
 // Coefficient storage: FP32 for complex64 input, FP16 for the reduced types.
 template <class In> struct Coef { using type = __half; };
 template <> struct Coef<InC32> { using type = float; };

@@ -154,9 +154,10 @@ ppf_gather_kernel(const PpfWork wl, const float2* __restrict__ tw, int* __restri
         }
 
         // coefficients of the owned channel pairs, in registers for the whole item
-        // (FP16 input keeps each tap's coefficients as one FP16 pair and
-        // multiplies FP16 samples directly: fma_f16_pair)
-        constexpr bool MIX = std::is_same<typename C::In, InC16>::value;
+        // (FP16 and int8 input keep each tap's coefficients as one FP16 pair
+        // and multiply FP16 samples directly, int8 turned into FP16 exactly:
+        // fma_f16_pair, f16_pairs)
+        constexpr bool MIX = !std::is_same<typename C::In, InC32>::value;
         float hr[MIX ? 1 : G][MIX ? 1 : T][2];
         uint32_t hq[MIX ? G : 1][MIX ? T : 1];
 #pragma unroll
@@ -207,10 +208,11 @@ ppf_gather_kernel(const PpfWork wl, const float2* __restrict__ tw, int* __restri
                     rr = rr >= RING_ROWS ? rr - RING_ROWS : rr;
                     const PV pv = *reinterpret_cast<const PV*>(ring + ((size_t)rr * NC + cl) * BPS);
                     if constexpr (MIX) {
+                        const uint2 xq = f16_pairs(pv);
 #pragma unroll
                         for (int i = 0; i < RBT; ++i) {
                             const int t = u - i;
-                            if (t >= 0 && t < T) fma_f16_pair(hq[g][t], pv, a0[i], a1[i]);
+                            if (t >= 0 && t < T) fma_f16_pair(hq[g][t], xq, a0[i], a1[i]);
                         }
                     } else {
                         float2 v0, v1;

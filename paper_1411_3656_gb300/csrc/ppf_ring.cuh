@@ -269,9 +269,10 @@ ppf_ring_kernel(const PpfWork wl, const float2* __restrict__ tw, int* __restrict
 
         // coefficients of this thread's channels, in FP32 registers (CPT = 1
         // keeps each as the pair (h, h))
-        // FP16 input with channel pairs keeps each tap's coefficients as one
-        // FP16 pair and multiplies FP16 samples directly (fma_f16_pair)
-        constexpr bool MIX = C::CPT == 2 && std::is_same<typename C::In, InC16>::value;
+        // FP16 and int8 input with channel pairs keep each tap's coefficients
+        // as one FP16 pair and multiply FP16 samples directly (int8 turned
+        // into FP16 exactly: fma_f16_pair, f16_pairs)
+        constexpr bool MIX = C::CPT == 2 && !std::is_same<typename C::In, InC32>::value;
         float hr[C::CPT == 2 && !MIX ? G : 1][C::CPT == 2 && !MIX ? T : 1][2];
         uint32_t hq[MIX ? G : 1][MIX ? T : 1];
         float2 hh[C::CPT == 1 ? G : 1][C::CPT == 1 ? T : 1];
@@ -326,10 +327,11 @@ ppf_ring_kernel(const PpfWork wl, const float2* __restrict__ tw, int* __restrict
                         rr = rr >= RING_ROWS ? rr - RING_ROWS : rr;
                         const PV pv = *reinterpret_cast<const PV*>(ring + ((size_t)rr * N + c) * BPS);
                         if constexpr (MIX) {
+                            const uint2 xq = f16_pairs(pv);
 #pragma unroll
                             for (int i = 0; i < RBT; ++i) {
                                 const int t = u - i;
-                                if (t >= 0 && t < T) fma_f16_pair(hq[g][t], pv, a0[i], a1[i]);
+                                if (t >= 0 && t < T) fma_f16_pair(hq[g][t], xq, a0[i], a1[i]);
                             }
                         } else {
                             float2 v0, v1;
