@@ -158,7 +158,12 @@ ppf_gather_kernel(const PpfWork wl, const float2* __restrict__ tw, int* __restri
         // and multiply FP16 samples directly, int8 turned into FP16 exactly:
         // fma_f16_pair, f16_pairs)
         constexpr bool MIX = !std::is_same<typename C::In, InC32>::value;
-        float hr[MIX ? 1 : G][MIX ? 1 : T][2];
+        // (complex64 with T <= 16 and at least 4 spectra per thread keeps each
+        // coefficient as (h, h) so that one packed FMA updates a complex
+        // accumulator, bitwise the scalar result)
+        constexpr bool PK = !MIX && T <= 16 && RBT >= 4;
+        float hr[MIX || PK ? 1 : G][MIX || PK ? 1 : T][2];
+        float2 hp[PK ? G : 1][PK ? T : 1][2];
         uint32_t hq[MIX ? G : 1][MIX ? T : 1];
 #pragma unroll
         for (int g = 0; g < G; ++g) {
@@ -167,6 +172,10 @@ ppf_gather_kernel(const PpfWork wl, const float2* __restrict__ tw, int* __restri
             for (int t = 0; t < T; ++t) {
                 if constexpr (MIX) {
                     hq[g][t] = *reinterpret_cast<const uint32_t*>(h + t * N + c);
+                } else if constexpr (PK) {
+                    const float v0 = coef_f(h[t * N + c]), v1 = coef_f(h[t * N + c + 1]);
+                    hp[g][t][0] = make_float2(v0, v0);
+                    hp[g][t][1] = make_float2(v1, v1);
                 } else {
                     hr[g][t][0] = coef_f(h[t * N + c]);
                     hr[g][t][1] = coef_f(h[t * N + c + 1]);
@@ -213,6 +222,17 @@ ppf_gather_kernel(const PpfWork wl, const float2* __restrict__ tw, int* __restri
                         for (int i = 0; i < RBT; ++i) {
                             const int t = u - i;
                             if (t >= 0 && t < T) fma_f16_pair(hq[g][t], xq, a0[i], a1[i]);
+                        }
+                    } else if constexpr (PK) {
+                        float2 v0, v1;
+                        Pair<typename C::In>::split(pv, v0, v1);
+#pragma unroll
+                        for (int i = 0; i < RBT; ++i) {
+                            const int t = u - i;
+                            if (t >= 0 && t < T) {
+                                a0[i] = __ffma2_rn(hp[g][t][0], v0, a0[i]);
+                                a1[i] = __ffma2_rn(hp[g][t][1], v1, a1[i]);
+                            }
                         }
                     } else {
                         float2 v0, v1;
