@@ -163,6 +163,33 @@ ppf_status_t ppf_stream_push(ppf_stream_t s, const void* d_chunk, int64_t n_samp
                              int64_t* n_spectra_out, void* stream);
 
 /*
+ * Checkpoint and resume of a stream.  A stream's whole state is its position
+ * (samples pushed, spectra emitted) and the samples it holds: the T-1 rows
+ * the next spectrum shares with the last one emitted plus the incomplete
+ * newest row (Section 2: every output needs the newest sample and T-1 past
+ * samples of its channel) -- fewer than T*N samples.
+ *
+ * ppf_stream_state_bytes -- bytes ppf_stream_save writes for the stream now:
+ *   a 48-byte header (magic "PPFS", version, N, T, dtype, pushed, emitted,
+ *   held) followed by the held samples in the plan's storage type.
+ * ppf_stream_save -- wait for the stream's pushes, then write its state into
+ *   the caller's host buffer h_state (capacity_bytes; PPF_ERR_INVALID_ARG if
+ *   smaller than ppf_stream_state_bytes).  The stream itself is unchanged
+ *   and may go on.
+ * ppf_stream_restore -- open a new stream on `plan` (same N, T and dtype as
+ *   the saved stream, else PPF_ERR_INVALID_ARG; any coefficients) from a
+ *   saved state; the history is uploaded on `stream` and the call returns
+ *   once it is on the device.  Pushes to the new stream continue exactly
+ *   where the saved one stopped: the spectra are those of an uninterrupted
+ *   stream.  A truncated or inconsistent state is PPF_ERR_INVALID_ARG.  The
+ *   caller owns h_state; close the new stream with ppf_stream_close.
+ */
+ppf_status_t ppf_stream_state_bytes(ppf_stream_t s, size_t* bytes);
+ppf_status_t ppf_stream_save(ppf_stream_t s, void* h_state, size_t capacity_bytes);
+ppf_status_t ppf_stream_restore(ppf_plan_t plan, const void* h_state, size_t bytes, ppf_stream_t* out,
+                                void* stream);
+
+/*
  * ppf_execute_noalloc -- the whole PPF with no plan and no device allocation.
  * The paper has no counterpart; this is for callers that cannot allocate
  * device memory when they need a filter bank: code running while a stream is

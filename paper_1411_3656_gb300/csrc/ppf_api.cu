@@ -428,6 +428,103 @@ ppf_status_t ppf_stream_push(ppf_stream_t s, const void* d_chunk, int64_t n_samp
     return PPF_OK;
 }
 
+// Saved stream state: this header, then the held samples in the plan's
+// storage type.  The held samples are the stream's samples from the first row
+// of spectrum `emitted` on (held = pushed - emitted*N < T*N).
+namespace {
+struct StreamStateHeader {
+    char magic[4];  // "PPFS"
+    int32_t version;
+    int32_t N, T, dtype, pad;
+    int64_t pushed, emitted, held;
+};
+constexpr int32_t kStreamStateVersion = 1;
+}  // namespace
+
+ppf_status_t ppf_stream_state_bytes(ppf_stream_t s, size_t* bytes)
+{
+    if (!s || !bytes) return PPF_ERR_INVALID_ARG;
+    *bytes = sizeof(StreamStateHeader) + (size_t)s->held * sample_bytes(s->plan->dtype);
+    return PPF_OK;
+}
+
+ppf_status_t ppf_stream_save(ppf_stream_t s, void* h_state, size_t capacity_bytes)
+{
+    if (!s || !h_state) return PPF_ERR_INVALID_ARG;
+    const int bps = sample_bytes(s->plan->dtype);
+    const size_t need = sizeof(StreamStateHeader) + (size_t)s->held * bps;
+    if (capacity_bytes < need) return PPF_ERR_INVALID_ARG;
+    if (pending_cuda_error()) return PPF_ERR_CUDA;
+    // the pushes enqueued so far must have written the history
+    cudaError_t e = s->last ? cudaStreamSynchronize(s->last) : cudaSuccess;
+    if (e != cudaSuccess) return from_cuda(e);
+    StreamStateHeader hd{};
+    std::memcpy(hd.magic, "PPFS", 4);
+    hd.version = kStreamStateVersion;
+    hd.N = s->plan->view.N;
+    hd.T = s->plan->view.T;
+    hd.dtype = (int32_t)s->plan->dtype;
+    hd.pushed = s->pushed;
+    hd.emitted = s->emitted;
+    hd.held = s->held;
+    std::memcpy(h_state, &hd, sizeof(hd));
+    if (s->held > 0)
+        e = cudaMemcpy(static_cast<char*>(h_state) + sizeof(hd), s->d_buf[s->cur], (size_t)s->held * bps,
+                       cudaMemcpyDeviceToHost);
+    return from_cuda(e);
+}
+
+ppf_status_t ppf_stream_restore(ppf_plan_t plan, const void* h_state, size_t bytes, ppf_stream_t* out,
+                                void* stream)
+{
+    if (!plan || !h_state || !out) return PPF_ERR_INVALID_ARG;
+    *out = nullptr;
+    if (plan->view.out_f16) return PPF_ERR_UNSUPPORTED;
+    if (bytes < sizeof(StreamStateHeader)) return PPF_ERR_INVALID_ARG;
+    StreamStateHeader hd;
+    std::memcpy(&hd, h_state, sizeof(hd));
+    const int64_t N = plan->view.N, T = plan->view.T;
+    const int bps = sample_bytes(plan->dtype);
+    // the state must be one a stream of this plan's N, T and dtype can be in
+    if (std::memcmp(hd.magic, "PPFS", 4) != 0 || hd.version != kStreamStateVersion || hd.N != N || hd.T != T ||
+        hd.dtype != (int32_t)plan->dtype || hd.pushed < 0)
+        return PPF_ERR_INVALID_ARG;
+    const int64_t complete = hd.pushed / N - T + 1 > 0 ? hd.pushed / N - T + 1 : 0;
+    if (hd.emitted != complete || hd.held != hd.pushed - hd.emitted * N || hd.held < 0 || hd.held >= T * N)
+        return PPF_ERR_INVALID_ARG;
+    if (bytes < sizeof(hd) + (size_t)hd.held * bps) return PPF_ERR_INVALID_ARG;
+    if (pending_cuda_error()) return PPF_ERR_CUDA;
+    ppf_stream_s* s = new (std::nothrow) ppf_stream_s();
+    if (!s) return PPF_ERR_OUT_OF_MEMORY;
+    s->plan = plan;
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    int64_t cap = (T + 1) * N;
+    while (cap < hd.held) cap *= 2;
+    cudaError_t e = cudaSuccess;
+    for (int i = 0; i < 2 && e == cudaSuccess; ++i) e = cudaMallocAsync(&s->d_buf[i], (size_t)cap * bps, st);
+    if (e == cudaSuccess && hd.held > 0)
+        e = cudaMemcpyAsync(s->d_buf[0], static_cast<const char*>(h_state) + sizeof(hd), (size_t)hd.held * bps,
+                            cudaMemcpyHostToDevice, st);
+    // the caller's buffer may be reused once this returns
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess) {
+        for (int i = 0; i < 2; ++i)
+            if (s->d_buf[i]) cudaFreeAsync(s->d_buf[i], st);
+        cudaStreamSynchronize(st);
+        delete s;
+        return from_cuda(e);
+    }
+    s->cap = cap;
+    s->cur = 0;
+    s->held = hd.held;
+    s->pushed = hd.pushed;
+    s->emitted = hd.emitted;
+    s->base = hd.emitted * N;
+    s->last = st;
+    *out = s;
+    return PPF_OK;
+}
+
 ppf_status_t ppf_stream_close(ppf_stream_t s)
 {
     if (!s) return PPF_ERR_INVALID_ARG;

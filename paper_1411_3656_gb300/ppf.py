@@ -30,6 +30,7 @@ FLAG_OUT_F16 = 4
 #: every entry point declared in include/ppf.h
 EXPORTS = ("ppf_plan_create", "ppf_plan_destroy", "ppf_execute", "ppf_execute_host",
            "ppf_stream_open", "ppf_stream_push", "ppf_stream_position", "ppf_stream_close",
+           "ppf_stream_state_bytes", "ppf_stream_save", "ppf_stream_restore",
            "ppf_status_string", "ppf_plan_kernel_name", "ppf_launch_count", "ppf_variant_count",
            "ppf_variant_name", "ppf_execute_noalloc", "ppf_batch_create", "ppf_batch_execute",
            "ppf_batch_launches", "ppf_batch_destroy", "ppf_server_create", "ppf_server_admit",
@@ -77,6 +78,9 @@ def load(path: str | None = None):
             "ppf_stream_push": ([vp, vp, i64, vp, i64, ctypes.POINTER(i64), vp], i32),
             "ppf_stream_position": ([vp, ctypes.POINTER(i64), ctypes.POINTER(i64)], i32),
             "ppf_stream_close": ([vp], i32),
+            "ppf_stream_state_bytes": ([vp, ctypes.POINTER(ctypes.c_size_t)], i32),
+            "ppf_stream_save": ([vp, vp, ctypes.c_size_t], i32),
+            "ppf_stream_restore": ([vp, vp, ctypes.c_size_t, ctypes.POINTER(vp), vp], i32),
             "ppf_status_string": ([i32], ctypes.c_char_p),
             "ppf_plan_kernel_name": ([vp], ctypes.c_char_p),
             "ppf_launch_count": ([], i64),
@@ -170,6 +174,22 @@ def ppf_stream_position(stream_obj: int):
 
 def ppf_stream_close(stream_obj: int):
     _check(load().ppf_stream_close(stream_obj), "ppf_stream_close")
+
+
+def ppf_stream_state_bytes(stream_obj: int) -> int:
+    n = ctypes.c_size_t(0)
+    _check(load().ppf_stream_state_bytes(stream_obj, ctypes.byref(n)), "ppf_stream_state_bytes")
+    return n.value
+
+
+def ppf_stream_save(stream_obj: int, h_state: int, capacity: int) -> int:
+    return load().ppf_stream_save(stream_obj, h_state, int(capacity))
+
+
+def ppf_stream_restore(plan: int, h_state: int, nbytes: int, cuda_stream: int = 0):
+    out = ctypes.c_void_p()
+    st = load().ppf_stream_restore(plan, h_state, int(nbytes), ctypes.byref(out), cuda_stream)
+    return st, out.value
 
 
 def ppf_status_string(status: int) -> str:
@@ -337,6 +357,26 @@ class Stream:
     @property
     def position(self):
         return ppf_stream_position(self.handle)
+
+    def save(self) -> bytes:
+        """The stream's state (position and held samples) as bytes; see ppf_stream_save."""
+        import numpy as np
+        n = ppf_stream_state_bytes(self.handle)
+        buf = np.empty(n, dtype=np.uint8)
+        _check(ppf_stream_save(self.handle, buf.ctypes.data, n), "ppf_stream_save")
+        return buf.tobytes()
+
+    @classmethod
+    def restore(cls, plan: "Plan", state: bytes, stream=None) -> "Stream":
+        """A new stream on ``plan`` that continues a saved one; see ppf_stream_restore."""
+        import numpy as np
+        buf = np.frombuffer(state, dtype=np.uint8)
+        st, handle = ppf_stream_restore(plan.handle, buf.ctypes.data, buf.size, _stream_ptr(stream))
+        _check(st, "ppf_stream_restore")
+        obj = cls.__new__(cls)
+        obj.plan = plan
+        obj.handle = handle
+        return obj
 
     def close(self):
         if self.handle:
