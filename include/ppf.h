@@ -357,6 +357,18 @@ int64_t ppf_launch_count(void);
  */
 ppf_status_t ppf_check_timeout(unsigned limit_us, void* stream);
 
+/*
+ * ppf_check_violations -- out-of-bounds accesses counted by the checked
+ * build of this library (compiled with -DPPF_CHECKED: every instrumented
+ * shared-memory and global access of the kernels first tests its index
+ * against its buffer, counts a violation and skips the access instead of
+ * making it).  Synchronises the device, returns the count since the last
+ * reset (reset != 0 clears it), -1 in the normal build (no checks compiled),
+ * -2 if the device could not be read.  The paper has no counterpart: this is
+ * test infrastructure standing in for a memory checker.
+ */
+int64_t ppf_check_violations(int reset);
+
 /* Window of the prototype low-pass filter (Section 2). */
 typedef enum {
     PPF_WINDOW_HAMMING = 0,    /* 0.54 - 0.46 cos(2 pi n / (L-1)) */

@@ -18,6 +18,10 @@ CSRC = os.path.join(HERE, "csrc")
 INCLUDE = os.path.join(ROOT, "include")
 BUILD = os.path.join(ROOT, "_build")
 LIB = os.path.join(HERE, "libppf.so")
+# the checked build (-DPPF_CHECKED): the same sources with every instrumented
+# kernel access bounds-checked and counted instead of made when out of range
+LIB_CHECKED = os.path.join(HERE, "libppf_checked.so")
+BUILD_CHECKED = os.path.join(ROOT, "_build_checked")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 NVCC_FLAGS = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "--expt-relaxed-constexpr",
               "-I" + INCLUDE, "-I" + CSRC]
@@ -39,23 +43,26 @@ def _deps():
                                + glob.glob(os.path.join(CSRC, "*.inc")) + glob.glob(os.path.join(INCLUDE, "*.h")))
 
 
-def up_to_date() -> bool:
-    if not os.path.exists(LIB):
+def up_to_date(lib: str = LIB) -> bool:
+    if not os.path.exists(lib):
         return False
-    t = os.path.getmtime(LIB)
+    t = os.path.getmtime(lib)
     return all(os.path.getmtime(d) <= t for d in _deps())
 
 
-def build(force: bool = False, verbose: bool = False, jobs: int | None = None, extra: list[str] | None = None) -> str:
-    if not force and up_to_date():
-        return LIB
-    os.makedirs(BUILD, exist_ok=True)
+def build(force: bool = False, verbose: bool = False, jobs: int | None = None, extra: list[str] | None = None,
+          checked: bool = False) -> str:
+    """Build libppf.so (or, with checked=True, libppf_checked.so) and return its path."""
+    lib, bdir = (LIB_CHECKED, BUILD_CHECKED) if checked else (LIB, BUILD)
+    if not force and up_to_date(lib):
+        return lib
+    os.makedirs(bdir, exist_ok=True)
     cc = nvcc()
-    flags = NVCC_FLAGS + (extra or [])
+    flags = NVCC_FLAGS + (["-DPPF_CHECKED"] if checked else []) + (extra or [])
     srcs = _sources()
 
     def compile_one(src):
-        obj = os.path.join(BUILD, os.path.basename(src) + ".o")
+        obj = os.path.join(bdir, os.path.basename(src) + ".o")
         cmd = [cc, "-c", src, "-o", obj] + ARCH + flags
         if verbose:
             print(" ".join(cmd), flush=True)
@@ -69,13 +76,13 @@ def build(force: bool = False, verbose: bool = False, jobs: int | None = None, e
     jobs = jobs or max(1, min(len(srcs), os.cpu_count() or 1))
     with ThreadPoolExecutor(jobs) as ex:
         objs = list(ex.map(compile_one, srcs))
-    tmp = LIB + f".{os.getpid()}.tmp"
+    tmp = lib + f".{os.getpid()}.tmp"
     cmd = [cc, "-shared", "-o", tmp] + objs + ARCH + ["-cudart", "shared"]
     r = subprocess.run(cmd, capture_output=True, text=True)
     if r.returncode != 0:
         raise RuntimeError(f"link failed:\n{r.stdout}\n{r.stderr}")
-    os.replace(tmp, LIB)
-    return LIB
+    os.replace(tmp, lib)
+    return lib
 
 
 if __name__ == "__main__":

@@ -1,5 +1,9 @@
-// Failure-detection self-check: the device-side bounded wait, made to run out.
+// Failure-detection self-check: the device-side bounded wait, made to run
+// out; and the violation counters of the checked (-DPPF_CHECKED) build.
 #include <cuda_runtime.h>
+
+#include <mutex>
+#include <vector>
 
 #include "../../include/ppf.h"
 #include "ppf_launch.h"
@@ -43,4 +47,46 @@ extern "C" ppf_status_t ppf_check_timeout(unsigned limit_us, void* stream)
     cudaFreeHost(h_err);
     if (e != cudaSuccess) return PPF_ERR_CUDA;
     return flagged ? PPF_ERR_TIMEOUT : PPF_OK;
+}
+
+namespace ppf {
+namespace {
+struct CheckRegistry {
+    std::mutex m;
+    std::vector<unsigned long long (*)(bool)> readers;
+};
+CheckRegistry& check_registry()
+{
+    static CheckRegistry r;
+    return r;
+}
+}  // namespace
+
+// Each translation unit of the checked build registers the reader of its
+// counter at load time.
+void register_check_counter(unsigned long long (*read)(bool reset))
+{
+    CheckRegistry& r = check_registry();
+    std::lock_guard<std::mutex> g(r.m);
+    r.readers.push_back(read);
+}
+}  // namespace ppf
+
+extern "C" int64_t ppf_check_violations(int reset)
+{
+#ifdef PPF_CHECKED
+    ppf::CheckRegistry& r = ppf::check_registry();
+    std::lock_guard<std::mutex> g(r.m);
+    if (cudaDeviceSynchronize() != cudaSuccess) return -2;
+    unsigned long long total = 0;
+    for (auto read : r.readers) {
+        const unsigned long long v = read(reset != 0);
+        if (v == ~0ull) return -2;
+        total += v;
+    }
+    return (int64_t)total;
+#else
+    (void)reset;
+    return -1;
+#endif
 }

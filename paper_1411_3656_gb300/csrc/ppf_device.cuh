@@ -19,6 +19,35 @@
 #include <cstdint>
 #include <type_traits>
 
+// ------------------------------------------------------------------ checked build
+// A debug build of the same sources with -DPPF_CHECKED (the tests' stand-in
+// for a memory checker) tests the index of every instrumented shared-memory
+// and global access against the buffer it addresses before making it.  A
+// violation is counted in the translation unit's ppf_check_count_d and the
+// access is skipped, so a wrong index shows as a count
+// (ppf_check_violations), not as a fault.  In the normal build PPF_INBOUNDS
+// is the constant true and the checks compile to nothing.
+#ifdef PPF_CHECKED
+static __device__ unsigned long long ppf_check_count_d;
+#define PPF_INBOUNDS(cond) ((cond) ? true : (atomicAdd(&ppf_check_count_d, 1ull), false))
+namespace ppf {
+void register_check_counter(unsigned long long (*read)(bool reset));
+}
+static unsigned long long ppf_read_check_count(bool reset)
+{
+    unsigned long long v = 0;
+    if (cudaMemcpyFromSymbol(&v, ppf_check_count_d, sizeof(v)) != cudaSuccess) return ~0ull;
+    if (reset) {
+        const unsigned long long z = 0;
+        cudaMemcpyToSymbol(ppf_check_count_d, &z, sizeof(z));
+    }
+    return v;
+}
+static const bool ppf_check_counter_registered = (ppf::register_check_counter(ppf_read_check_count), true);
+#else
+#define PPF_INBOUNDS(cond) true
+#endif
+
 namespace ppf {
 
 // ------------------------------------------------------------------ complex

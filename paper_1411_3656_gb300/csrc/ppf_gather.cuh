@@ -142,8 +142,10 @@ ppf_gather_kernel(const PpfWork wl, const float2* __restrict__ tw, int* __restri
             const int64_t r0 = s_lo + (int64_t)k * ROWS;
             const int nrows = (int)(in_end - r0 < ROWS ? in_end - r0 : ROWS);
             const int slot = (cbase + k) % NCH;
-            mbar_arrive_expect_tx(&bars[slot], (uint32_t)(nrows * C::SEG_BYTES));
-            for (int q = 0; q < nrows; ++q)
+            // (copies the checked build refuses complete the phase with no bytes)
+            const bool ok = PPF_INBOUNDS(slot * C::CHUNK_BYTES + nrows * C::SEG_BYTES <= C::RING_BYTES);
+            mbar_arrive_expect_tx(&bars[slot], ok ? (uint32_t)(nrows * C::SEG_BYTES) : 0u);
+            for (int q = 0; q < (ok ? nrows : 0); ++q)
                 tma_load_1d(ring + slot * C::CHUNK_BYTES + q * C::SEG_BYTES, x + (r0 + q) * N + rank * NC,
                             (uint32_t)C::SEG_BYTES, &bars[slot], policy);
         };
@@ -215,7 +217,10 @@ ppf_gather_kernel(const PpfWork wl, const float2* __restrict__ tw, int* __restri
                 for (int u = 0; u < RBT + T - 1; ++u) {
                     int rr = rrb + i0 + u;
                     rr = rr >= RING_ROWS ? rr - RING_ROWS : rr;
-                    const PV pv = *reinterpret_cast<const PV*>(ring + ((size_t)rr * NC + cl) * BPS);
+                    const size_t ro = ((size_t)rr * NC + cl) * BPS;
+                    const PV pv = PPF_INBOUNDS(ro + sizeof(PV) <= (size_t)C::RING_BYTES)
+                                      ? *reinterpret_cast<const PV*>(ring + ro)
+                                      : PV{};
                     if constexpr (MIX) {
                         const uint2 xq = f16_pairs(pv);
 #pragma unroll
@@ -254,7 +259,8 @@ ppf_gather_kernel(const PpfWork wl, const float2* __restrict__ tw, int* __restri
                     for (int i = 0; i < RBT; ++i) {
                         const int row = i0 + i, q = row / RB, rr = row % RB;
                         const uint32_t off = (uint32_t)((rr * C::RS + rank * NC + cl) * 8);
-                        st_async_f4(map_shared_rank(xbase + off, (uint32_t)q),
+                        if (PPF_INBOUNDS(off + 16 <= (uint32_t)C::X_SLOTS * 8 && q < P))
+                            st_async_f4(map_shared_rank(xbase + off, (uint32_t)q),
                                     make_float4(a0[i].x, a0[i].y, a1[i].x, a1[i].y),
                                     map_shared_rank(fullbase, (uint32_t)q));
                     }

@@ -123,7 +123,8 @@ ppf_generic_kernel(const typename In::raw* __restrict__ x,
                     o[1] = a1;
                 }
             } else {
-                *reinterpret_cast<float4*>(buf + row * RS + c) = make_float4(a0.x, a0.y, a1.x, a1.y);
+                if (PPF_INBOUNDS(row * RS + c + 2 <= RB * RS))
+                    *reinterpret_cast<float4*>(buf + row * RS + c) = make_float4(a0.x, a0.y, a1.x, a1.y);
             }
         }
         if (fir_only) continue;

@@ -88,22 +88,27 @@ __device__ __forceinline__ void fft_pass_pp(const float2* in, float2* out, const
         if (NB % NT == 0 || b < NB) {
             const int row = b / BPR, j = b % BPR;
             float2 v[R];
-            const float2* bi = in + row * RS + (IN_NS == 0 ? j : pad_slot<IN_NS, IN_R>(j));
+            const int bx = row * RS + (IN_NS == 0 ? j : pad_slot<IN_NS, IN_R>(j));
 #pragma unroll
-            for (int r = 0; r < R; ++r) v[r] = bi[r * (IN_NS == 0 ? N / R : pad_stride<IN_NS, IN_R, N / R>())];
+            for (int r = 0; r < R; ++r) {
+                const int ix = bx + r * (IN_NS == 0 ? N / R : pad_stride<IN_NS, IN_R, N / R>());
+                v[r] = PPF_INBOUNDS(ix < RB * RS) ? in[ix] : make_float2(0.f, 0.f);
+            }
             if constexpr (P > 0) apply_twiddles<R>(tw.template get<P>(), v);
             dft<R>(v);
             if constexpr (LAST) {
                 if (row < rows) {
                     OT* o = Yb + (int64_t)row * N + j;
 #pragma unroll
-                    for (int q = 0; q < R; ++q) st_bin(o + q * NS, v[q]);
+                    for (int q = 0; q < R; ++q)
+                        if (PPF_INBOUNDS(j + q * NS < N)) st_bin(o + q * NS, v[q]);
                 }
             } else {
                 // the R outputs lie in one padding group: one slot computation
-                float2* bo = out + row * RS + pad_slot<NS, R>((j / NS) * NS * R + (j % NS));
+                const int ox = row * RS + pad_slot<NS, R>((j / NS) * NS * R + (j % NS));
 #pragma unroll
-                for (int q = 0; q < R; ++q) bo[q * NS] = v[q];
+                for (int q = 0; q < R; ++q)
+                    if (PPF_INBOUNDS(ox + q * NS < RB * RS)) out[ox + q * NS] = v[q];
             }
         }
     }
@@ -144,9 +149,12 @@ __device__ __forceinline__ void fft_pass_ip(float2* buf, const PassTwiddlesR<N, 
         const int b = threadIdx.x + k * NT;
         if (NB % NT == 0 || b < NB) {
             const int row = b / BPR, j = b % BPR;
-            const float2* bi = buf + row * RS + (IN_NS == 0 ? j : pad_slot<IN_NS, IN_R>(j));
+            const int bx = row * RS + (IN_NS == 0 ? j : pad_slot<IN_NS, IN_R>(j));
 #pragma unroll
-            for (int r = 0; r < R; ++r) v[k][r] = bi[r * (IN_NS == 0 ? N / R : pad_stride<IN_NS, IN_R, N / R>())];
+            for (int r = 0; r < R; ++r) {
+                const int ix = bx + r * (IN_NS == 0 ? N / R : pad_stride<IN_NS, IN_R, N / R>());
+                v[k][r] = PPF_INBOUNDS(ix < RB * RS) ? buf[ix] : make_float2(0.f, 0.f);
+            }
         }
     }
     __syncthreads();
@@ -162,12 +170,14 @@ __device__ __forceinline__ void fft_pass_ip(float2* buf, const PassTwiddlesR<N, 
                 if (row < rows) {
                     OT* o = Yb + (int64_t)row * N + j;
 #pragma unroll
-                    for (int q = 0; q < R; ++q) st_bin(o + q * NS, v[k][q]);
+                    for (int q = 0; q < R; ++q)
+                        if (PPF_INBOUNDS(j + q * NS < N)) st_bin(o + q * NS, v[k][q]);
                 }
             } else {
-                float2* bo = buf + row * RS + pad_slot<NS, R>((j / NS) * NS * R + (j % NS));
+                const int ox = row * RS + pad_slot<NS, R>((j / NS) * NS * R + (j % NS));
 #pragma unroll
-                for (int q = 0; q < R; ++q) bo[q * NS] = v[k][q];
+                for (int q = 0; q < R; ++q)
+                    if (PPF_INBOUNDS(ox + q * NS < RB * RS)) buf[ox + q * NS] = v[k][q];
             }
         }
     }
@@ -258,8 +268,10 @@ ppf_ring_kernel(const PpfWork wl, const float2* __restrict__ tw, int* __restrict
             const int64_t rows = in_end - r0 < RB ? in_end - r0 : RB;
             const uint32_t bytes = (uint32_t)(rows * N * BPS);
             const int slot = (cbase + k) % NCH;
-            mbar_arrive_expect_tx(&bars[slot], bytes);
-            tma_load_1d(ring + slot * C::CHUNK_BYTES, x + r0 * N, bytes, &bars[slot], policy);
+            // (a copy the checked build refuses completes the phase with no bytes)
+            const bool ok = PPF_INBOUNDS((size_t)slot * C::CHUNK_BYTES + bytes <= (size_t)C::RING_BYTES);
+            mbar_arrive_expect_tx(&bars[slot], ok ? bytes : 0u);
+            if (ok) tma_load_1d(ring + slot * C::CHUNK_BYTES, x + r0 * N, bytes, &bars[slot], policy);
         };
         if (tid == 0) {
             const int first = nchunks < NCH ? nchunks : NCH;
@@ -336,7 +348,10 @@ ppf_ring_kernel(const PpfWork wl, const float2* __restrict__ tw, int* __restrict
                     for (int u = 0; u < RBT + T - 1; ++u) {
                         int rr = rrb + i0 + u;
                         rr = rr >= RING_ROWS ? rr - RING_ROWS : rr;
-                        const PV pv = *reinterpret_cast<const PV*>(ring + ((size_t)rr * N + c) * BPS);
+                        const size_t ro = ((size_t)rr * N + c) * BPS;
+                        const PV pv = PPF_INBOUNDS(ro + sizeof(PV) <= (size_t)C::RING_BYTES)
+                                          ? *reinterpret_cast<const PV*>(ring + ro)
+                                          : PV{};
                         if constexpr (MIX) {
                             const uint2 xq = f16_pairs(pv);
 #pragma unroll
@@ -372,8 +387,9 @@ ppf_ring_kernel(const PpfWork wl, const float2* __restrict__ tw, int* __restrict
                     }
 #pragma unroll
                     for (int i = 0; i < RBT; ++i)
-                        *reinterpret_cast<float4*>(fb + (i0 + i) * RS + c) =
-                            make_float4(a0[i].x, a0[i].y, a1[i].x, a1[i].y);
+                        if (PPF_INBOUNDS((i0 + i) * RS + c + 2 <= C::BUF_SLOTS))
+                            *reinterpret_cast<float4*>(fb + (i0 + i) * RS + c) =
+                                make_float4(a0[i].x, a0[i].y, a1[i].x, a1[i].y);
                 } else {
                     float2 a[RBT];
 #pragma unroll
@@ -382,7 +398,10 @@ ppf_ring_kernel(const PpfWork wl, const float2* __restrict__ tw, int* __restrict
                     for (int u = 0; u < RBT + T - 1; ++u) {
                         int rr = rrb + i0 + u;
                         rr = rr >= RING_ROWS ? rr - RING_ROWS : rr;
-                        const float2 v = decode(*reinterpret_cast<const raw*>(ring + ((size_t)rr * N + c) * BPS));
+                        const size_t ro = ((size_t)rr * N + c) * BPS;
+                        const float2 v = PPF_INBOUNDS(ro + sizeof(raw) <= (size_t)C::RING_BYTES)
+                                             ? decode(*reinterpret_cast<const raw*>(ring + ro))
+                                             : make_float2(0.f, 0.f);
 #pragma unroll
                         for (int i = 0; i < RBT; ++i) {
                             const int t = u - i;
@@ -390,7 +409,8 @@ ppf_ring_kernel(const PpfWork wl, const float2* __restrict__ tw, int* __restrict
                         }
                     }
 #pragma unroll
-                    for (int i = 0; i < RBT; ++i) fb[(i0 + i) * RS + c] = a[i];
+                    for (int i = 0; i < RBT; ++i)
+                        if (PPF_INBOUNDS((i0 + i) * RS + c + 1 <= C::BUF_SLOTS)) fb[(i0 + i) * RS + c] = a[i];
                 }
             }
             if (__syncthreads_or(failed)) {

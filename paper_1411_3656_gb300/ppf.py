@@ -16,7 +16,9 @@ import os
 import threading
 
 HERE = os.path.dirname(os.path.abspath(__file__))
-LIB_PATH = os.path.join(HERE, "libppf.so")
+# PPF_LIBRARY selects another build of the same library (the tests point it
+# at the bounds-checked build, libppf_checked.so)
+LIB_PATH = os.environ.get("PPF_LIBRARY") or os.path.join(HERE, "libppf.so")
 
 PPF_OK = 0
 STATUS = {0: "PPF_OK", 1: "PPF_ERR_INVALID_ARG", 2: "PPF_ERR_UNSUPPORTED", 3: "PPF_ERR_MISALIGNED",
@@ -35,7 +37,8 @@ EXPORTS = ("ppf_plan_create", "ppf_plan_destroy", "ppf_execute", "ppf_execute_ho
            "ppf_variant_name", "ppf_execute_noalloc", "ppf_batch_create", "ppf_batch_execute",
            "ppf_batch_launches", "ppf_batch_destroy", "ppf_server_create", "ppf_server_admit",
            "ppf_server_release", "ppf_server_submit", "ppf_server_submit_many", "ppf_server_tick", "ppf_server_position",
-           "ppf_server_info", "ppf_server_destroy", "ppf_design_coeffs", "ppf_check_timeout")
+           "ppf_server_info", "ppf_server_destroy", "ppf_design_coeffs", "ppf_check_timeout",
+           "ppf_check_violations")
 
 
 class PPFJob(ctypes.Structure):
@@ -102,6 +105,7 @@ def load(path: str | None = None):
             "ppf_server_destroy": ([vp], i32),
             "ppf_design_coeffs": ([i32, i32, i32, ctypes.c_double, ctypes.POINTER(ctypes.c_float)], i32),
             "ppf_check_timeout": ([ctypes.c_uint, vp], i32),
+            "ppf_check_violations": ([i32], i64),
         }
         for name, (args, res) in sig.items():
             fn = getattr(lib, name)

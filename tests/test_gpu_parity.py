@@ -63,7 +63,7 @@ def test_plain_config_n256_t8_s1024(ppf):
 
 SIZES = [(4, 1, 37), (4, 3, 50), (8, 2, 41), (16, 4, 33), (32, 5, 70), (64, 8, 39), (128, 4, 77),
          (256, 8, 45), (256, 1, 19), (512, 16, 21), (1024, 8, 19), (1024, 32, 9), (2048, 4, 11),
-         (4096, 8, 7), (4096, 32, 5), (256, 64, 13), (128, 13, 29)]
+         (4096, 8, 7), (4096, 32, 5), (256, 64, 13), (128, 13, 29), (4096, 64, 3), (4, 64, 20)]
 
 
 @pytest.mark.parametrize("N,T,S", SIZES)
