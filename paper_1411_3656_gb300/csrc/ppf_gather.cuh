@@ -156,14 +156,14 @@ ppf_gather_kernel(const PpfWork wl, const float2* __restrict__ tw, int* __restri
         }
 
         // coefficients of the owned channel pairs, in registers for the whole item
-        // (FP16 and int8 input keep each tap's coefficients as one FP16 pair
-        // and multiply FP16 samples directly, int8 turned into FP16 exactly:
-        // fma_f16_pair, f16_pairs)
-        constexpr bool MIX = !std::is_same<typename C::In, InC32>::value;
-        // (complex64 with T <= 16 and at least 4 spectra per thread keeps each
-        // coefficient as (h, h) so that one packed FMA updates a complex
-        // accumulator, bitwise the scalar result)
-        constexpr bool PK = !MIX && T <= 16 && RBT >= 4;
+        // (channel pairs with G*T <= 32 and at least 4 spectra per thread, of
+        // any input type, keep each coefficient as (h, h) so that one packed
+        // FMA updates a complex accumulator -- bitwise the scalar result;
+        // otherwise FP16 and int8 input keep each tap's coefficients as one
+        // FP16 pair and multiply FP16 samples directly, int8 turned into FP16
+        // exactly: fma_f16_pair, f16_pairs)
+        constexpr bool PK = G * T <= 32 && RBT >= 4;
+        constexpr bool MIX = !PK && !std::is_same<typename C::In, InC32>::value;
         float hr[MIX || PK ? 1 : G][MIX || PK ? 1 : T][2];
         float2 hp[PK ? G : 1][PK ? T : 1][2];
         uint32_t hq[MIX ? G : 1][MIX ? T : 1];

@@ -8,7 +8,7 @@ static int variants_impl(int N, int T, int want, KernelEntry* out)
 {
     int idx = 0;
     PPF_GV(4096, 8, 2, 256, 1, 6, 1) PPF_GV(2048, 16, 2, 256, 2, 6, 1) PPF_GV(1024, 32, 2, 256, 4, 6, 1)
-    PPF_GV(4096, 16, 4, 256, 1, 6, 1) PPF_GV(4096, 32, 8, 256, 1, 6, 1)
+    PPF_GV(4096, 16, 4, 256, 1, 6, 1) PPF_GV(4096, 32, 8, 256, 1, 6, 1) PPF_GV(2048, 32, 4, 256, 2, 6, 1)
     return idx;
 }
 
@@ -23,7 +23,7 @@ static int variants_f16_impl(int N, int T, int want, KernelEntry* out)
 {
     int idx = 0;
     PPF_GVF(4096, 8, 2, 256, 1, 6, 1) PPF_GVF(2048, 16, 2, 256, 2, 6, 1) PPF_GVF(1024, 32, 2, 256, 4, 6, 1)
-    PPF_GVF(4096, 16, 4, 256, 1, 6, 1) PPF_GVF(4096, 32, 8, 256, 1, 6, 1)
+    PPF_GVF(4096, 16, 4, 256, 1, 6, 1) PPF_GVF(4096, 32, 8, 256, 1, 6, 1) PPF_GVF(2048, 32, 4, 256, 2, 6, 1)
     return idx;
 }
 

@@ -285,12 +285,12 @@ ppf_ring_kernel(const PpfWork wl, const float2* __restrict__ tw, int* __restrict
         // as one FP16 pair and multiply FP16 samples directly (int8 turned
         // into FP16 exactly: fma_f16_pair, f16_pairs)
         constexpr bool MIX = C::CPT == 2 && !std::is_same<typename C::In, InC32>::value;
-        // complex64 channel pairs with T <= 16 and at least 4 spectra per
-        // thread keep each coefficient as (h, h) so that one packed FMA
-        // updates a complex accumulator (half the FIR instructions, bitwise
-        // the scalar result; 4T registers per pair: measured slower with
-        // fewer spectra per thread, where the loads dominate)
-        constexpr bool PK = C::CPT == 2 && !MIX && T <= 16 && RBT >= 4;
+        // complex64 channel pairs with G*T <= 32 (at most 128 coefficient
+        // registers) and at least 4 spectra per thread keep each coefficient
+        // as (h, h) so that one packed FMA updates a complex accumulator (half
+        // the FIR instructions, bitwise the scalar result; measured slower
+        // with fewer spectra per thread, where the loads dominate)
+        constexpr bool PK = C::CPT == 2 && !MIX && G * T <= 32 && RBT >= 4;
         float hr[C::CPT == 2 && !MIX && !PK ? G : 1][C::CPT == 2 && !MIX && !PK ? T : 1][2];
         float2 hp[PK ? G : 1][PK ? T : 1][2];
         uint32_t hq[MIX ? G : 1][MIX ? T : 1];

@@ -18,10 +18,17 @@ def ppf():
 
 
 def _jobs(ppf, specs, seed):
-    """specs: (N, T, dtype, S).  Each job gets its own seeded input and h."""
+    """specs: (N, T, dtype, S[, kernel family]).  Each job gets its own seeded
+    input and h; a job naming a kernel family runs that family's first compiled
+    tile shape instead of the tuned default."""
     import torch
     out = []
-    for i, (N, T, dt, S) in enumerate(specs):
+    for i, spec in enumerate(specs):
+        N, T, dt, S = spec[:4]
+        flags = 0
+        if len(spec) > 4:
+            names = [ppf.ppf_variant_name(N, T, dt, v) for v in range(ppf.ppf_variant_count(N, T, dt))]
+            flags = ppf.flag_variant(next(v for v, nm in enumerate(names) if nm.startswith(spec[4])))
         g = np.random.default_rng(seed + i)
         h = g.standard_normal(N * T).astype(np.float32)
         x = synth.stream(synth.samples_for(S, N, T), N, seed + 100 + i)
@@ -29,7 +36,7 @@ def _jobs(ppf, specs, seed):
             x = synth.to_fp16_iq(x)
         elif dt == "ci8":
             x = synth.int8_iq(synth.samples_for(S, N, T), seed + 200 + i)
-        plan = ppf.Plan(N, T, h, dt)
+        plan = ppf.Plan(N, T, h, dt, flags)
         xd = torch.from_numpy(np.ascontiguousarray(x)).cuda()
         yd = torch.full((S, N), float("nan"), dtype=torch.complex64, device="cuda")
         out.append((plan, xd, yd, S))
@@ -37,7 +44,8 @@ def _jobs(ppf, specs, seed):
 
 
 SPECS = [(256, 8, "c32", 700), (256, 8, "c32", 1500), (1024, 8, "c32", 333), (4096, 16, "c32", 41),
-         (4096, 16, "c32", 9), (2048, 32, "c32", 17), (64, 5, "c32", 90), (128, 4, "c32", 257),
+         (4096, 16, "c32", 9), (2048, 32, "c32", 17, "cluster"), (2048, 32, "c32", 23), (64, 5, "c32", 90),
+         (128, 4, "c32", 257),
          (1024, 16, "c16", 120), (512, 8, "ci8", 77), (256, 4, "c32", 0), (2048, 8, "c32", 1)]
 
 
@@ -47,7 +55,7 @@ def test_batch_equals_individual(ppf, graph):
     jobs = _jobs(ppf, SPECS, 5000)
     batch = ppf.Batch(jobs, graph=graph)
     kernels = {p.kernel for p, _, _, _ in jobs}
-    assert any(k.startswith("ring") for k in kernels) and any(k.startswith("cluster") for k in kernels)
+    assert all(any(k.startswith(f) for k in kernels) for f in ("ring", "gather", "cluster"))
     before = ppf.ppf_launch_count()
     batch.execute()
     torch.cuda.synchronize()
