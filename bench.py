@@ -423,6 +423,18 @@ def run_ours(args):
                 "traffic": measured_traffic(args.workload, dtype, f'traffic_bytes_{dom["N"]}x{dom["T"]}')
                 if full_size else None}
 
+    # The dominant launch is bound on chip (FP32 issue and latency), not by HBM:
+    # its nominal arithmetic (4T + 5 log2 N flop per output sample) against the
+    # FP32 peak of this GPU at the SM clock sampled under load (SMs x 128 FP32
+    # lanes x 2 flop per FMA x clock).
+    sm_mhz = (clock or {}).get("sm_mhz") or 2070.0
+    n_sm = torch.cuda.get_device_properties(dev).multi_processor_count
+    fp32_peak = n_sm * 128 * 2 * sm_mhz * 1e6 / 1e12
+    dom_tflops = metrics.flops(dom["N"], dom["T"], dom["S"]) / (dom["ms"] / 1e3) / 1e12
+    dominant["alu"] = {"bound": "alu", "achieved": round(dom_tflops, 2), "peak": round(fp32_peak, 1),
+                       "unit": "TFLOP/s", "frac": round(dom_tflops / fp32_peak, 4),
+                       "peak_source": f"{n_sm} SMs x 128 FP32 lanes x 2 flop x {sm_mhz:.0f} MHz (sampled)"}
+
     # e2e through the public host-buffer entry point (pinned memory, copies inside)
     e2e = None
     if not args.no_e2e and args.out_dtype == "c64":  # host-buffer entry point: complex64 output only

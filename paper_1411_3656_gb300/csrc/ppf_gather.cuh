@@ -203,7 +203,30 @@ ppf_gather_kernel(const PpfWork wl, const float2* __restrict__ tw, int* __restri
             if (gk >= 1 && !failed && !mbar_wait_cluster_bounded(xfree, (uint32_t)((gk - 1) & 1))) failed = true;
             if (tid == 0) mbar_arrive_expect_tx(xfull, (uint32_t)C::XBYTES);
 
-            // 2. FIR over the ring; row i of the round goes to CTA i / RB
+            // 2. FIR over the ring; row i of the round goes to CTA i / RB.
+            //    With one row group the window starts at a chunk boundary:
+            //    row u lies in the window's chunk u / ROWS at row u % ROWS, so
+            //    the chunk bases are computed once per round and every load
+            //    is a base plus a compile-time offset.
+            constexpr int NW = (RBT + T - 2) / ROWS + 1;  // chunks the window spans
+            uint32_t cbase_off[C::RG == 1 ? NW : 1];
+            if constexpr (C::RG == 1) {
+#pragma unroll
+                for (int w = 0; w < NW; ++w) {
+                    int sl = rrb / ROWS + w;
+                    sl -= sl >= NCH ? NCH : 0;
+                    cbase_off[w] = (uint32_t)(sl * C::CHUNK_BYTES);
+                }
+            }
+            auto ring_off = [&](int u, int cl) -> size_t {
+                if constexpr (C::RG == 1) {
+                    return (size_t)cbase_off[u / ROWS] + ((size_t)(u % ROWS) * NC + cl) * BPS;
+                } else {
+                    int rr = rrb + i0 + u;
+                    rr = rr >= RING_ROWS ? rr - RING_ROWS : rr;
+                    return ((size_t)rr * NC + cl) * BPS;
+                }
+            };
 #pragma unroll
             for (int g = 0; g < G; ++g) {
                 const int cl = 2 * (pbase + g * NT);
@@ -215,9 +238,7 @@ ppf_gather_kernel(const PpfWork wl, const float2* __restrict__ tw, int* __restri
                 }
 #pragma unroll
                 for (int u = 0; u < RBT + T - 1; ++u) {
-                    int rr = rrb + i0 + u;
-                    rr = rr >= RING_ROWS ? rr - RING_ROWS : rr;
-                    const size_t ro = ((size_t)rr * NC + cl) * BPS;
+                    const size_t ro = ring_off(u, cl);
                     const PV pv = PPF_INBOUNDS(ro + sizeof(PV) <= (size_t)C::RING_BYTES)
                                       ? *reinterpret_cast<const PV*>(ring + ro)
                                       : PV{};

@@ -333,7 +333,31 @@ ppf_ring_kernel(const PpfWork wl, const float2* __restrict__ tw, int* __restrict
             float2* const fb = (ODD && (bcount & 1)) ? bufB : bufA;  // FIR output, FFT pass 0 input
             float2* const ob = (ODD && (bcount & 1)) ? bufA : bufB;
 
-            // 2. FIR over the ring (Eq. 1), RBT spectra x CPT channels per unit
+            // 2. FIR over the ring (Eq. 1), RBT spectra x CPT channels per unit.
+            //    With one row group the window starts at a chunk boundary, so
+            //    row u lies in the window's chunk u / RB at row u % RB: the
+            //    chunk bases are computed once per block and every load is a
+            //    base plus a compile-time offset (no per-row wrap test).
+            constexpr int NW = (RBT + T - 2) / RB + 1;  // chunks the window spans
+            uint32_t cbase_off[C::RG == 1 ? NW : 1];
+            if constexpr (C::RG == 1) {
+#pragma unroll
+                for (int w = 0; w < NW; ++w) {
+                    int sl = rrb / RB + w;
+                    sl -= sl >= NCH ? NCH : 0;
+                    cbase_off[w] = (uint32_t)(sl * C::CHUNK_BYTES);
+                }
+            }
+            // byte offset in the ring of window row u for channel (pair) c
+            auto ring_off = [&](int u, int c) -> size_t {
+                if constexpr (C::RG == 1) {
+                    return (size_t)cbase_off[u / RB] + ((size_t)(u % RB) * N + c) * BPS;
+                } else {
+                    int rr = rrb + i0 + u;
+                    rr = rr >= RING_ROWS ? rr - RING_ROWS : rr;
+                    return ((size_t)rr * N + c) * BPS;
+                }
+            };
 #pragma unroll
             for (int g = 0; g < G; ++g) {
                 const int c = C::CPT * (pbase + g * NT);
@@ -346,9 +370,7 @@ ppf_ring_kernel(const PpfWork wl, const float2* __restrict__ tw, int* __restrict
                     }
 #pragma unroll
                     for (int u = 0; u < RBT + T - 1; ++u) {
-                        int rr = rrb + i0 + u;
-                        rr = rr >= RING_ROWS ? rr - RING_ROWS : rr;
-                        const size_t ro = ((size_t)rr * N + c) * BPS;
+                        const size_t ro = ring_off(u, c);
                         const PV pv = PPF_INBOUNDS(ro + sizeof(PV) <= (size_t)C::RING_BYTES)
                                           ? *reinterpret_cast<const PV*>(ring + ro)
                                           : PV{};
@@ -396,9 +418,7 @@ ppf_ring_kernel(const PpfWork wl, const float2* __restrict__ tw, int* __restrict
                     for (int i = 0; i < RBT; ++i) a[i] = make_float2(0.f, 0.f);
 #pragma unroll
                     for (int u = 0; u < RBT + T - 1; ++u) {
-                        int rr = rrb + i0 + u;
-                        rr = rr >= RING_ROWS ? rr - RING_ROWS : rr;
-                        const size_t ro = ((size_t)rr * N + c) * BPS;
+                        const size_t ro = ring_off(u, c);
                         const float2 v = PPF_INBOUNDS(ro + sizeof(raw) <= (size_t)C::RING_BYTES)
                                              ? decode(*reinterpret_cast<const raw*>(ring + ro))
                                              : make_float2(0.f, 0.f);

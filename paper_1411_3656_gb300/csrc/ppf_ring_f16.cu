@@ -13,7 +13,7 @@ static int variants_impl(int N, int T, int want, KernelEntry* out)
     PPF_RVF(128, 16, 256, 16, 3, 2, 2, 16) PPF_RVF(128, 32, 256, 32, 4, 1, 2, 16)
     PPF_RVF(256, 4, 512, 16, 4, 1, 2, 16) PPF_RVF(256, 8, 256, 16, 4, 1, 1, 16)
     PPF_RVF(256, 16, 256, 8, 4, 2, 1, 16) PPF_RVF(256, 32, 256, 16, 4, 1, 1, 16)
-    PPF_RVF(512, 4, 256, 4, 3, 2, 2, 16) PPF_RVF(512, 8, 256, 4, 4, 2, 2, 8)
+    PPF_RVF(512, 4, 256, 4, 3, 2, 2, 16) PPF_RVF(512, 8, 256, 4, 4, 2, 2, 16)
     PPF_RVF(512, 16, 512, 8, 4, 1, 1, 16) PPF_RVFS(512, 32, 256, 8, 6, 1, 2)
     PPF_RVF(1024, 4, 256, 2, 4, 2, 2, 16) PPF_RVF(1024, 8, 256, 4, 4, 1, 2, 16)
     PPF_RVFS(1024, 16, 256, 4, 6, 1, 2)
