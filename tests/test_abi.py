@@ -58,3 +58,16 @@ def test_unsupported_sizes_rejected_before_any_device_call(lib):
     assert lib.ppf_stream_close(None) == 1
     assert lib.ppf_plan_kernel_name(None) is None
     assert ppf.ppf_launch_count() >= 0
+
+
+def test_stream_state_and_checker_entry_points_without_a_device(lib):
+    """Argument errors of the checkpoint entry points come back before any device
+    call; the normal build reports that it has no bounds checks compiled in."""
+    import ctypes
+    n = ctypes.c_size_t(0)
+    buf = (ctypes.c_ubyte * 64)()
+    assert lib.ppf_stream_state_bytes(None, ctypes.byref(n)) == 1
+    assert lib.ppf_stream_save(None, buf, 64) == 1
+    out = ctypes.c_void_p()
+    assert lib.ppf_stream_restore(None, buf, 64, ctypes.byref(out), None) == 1
+    assert lib.ppf_check_violations(0) == -1
