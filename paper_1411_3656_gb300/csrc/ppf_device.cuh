@@ -375,22 +375,24 @@ __host__ __device__ constexpr int fft_row_stride(int N) { return N + (N / 16 > 2
 // in the 16 eight-byte bank slots; padding NS slots after every NS*R
 // elements spreads them over distinct slots while the next pass's reads (16
 // consecutive elements from a 16-aligned start) stay contiguous.
-template <int NS, int R>
+// PD > 1 pads NS slots after every PD*NS*R elements instead (less room, at
+// the price of PD-way conflicts in the writes of passes with NS < 16).
+template <int NS, int R, int PD = 1>
 __device__ __forceinline__ int pad_slot(int idx)
 {
     if constexpr (NS >= 16 || NS * R < 2) return idx;
-    else return idx + NS * (idx / (NS * R));
+    else return idx + NS * (idx / (PD * NS * R));
 }
 
 // Slots from element j to element j + L of a buffer written by a pass (NS, R),
 // for L a multiple of NS*R: the padding grows by L/R, so the R inputs of a
 // butterfly (j + r*L) sit at fixed offsets from pad_slot(j) and their
 // addresses need no per-element division.
-template <int NS, int R, int L>
+template <int NS, int R, int L, int PD = 1>
 __host__ __device__ constexpr int pad_stride()
 {
-    static_assert(NS * R < 2 || L % (NS * R) == 0, "stride must span whole padding groups");
-    return (NS >= 16 || NS * R < 2) ? L : L + L / R;
+    static_assert(NS >= 16 || NS * R < 2 || L % (PD * NS * R) == 0, "stride must span whole padding groups");
+    return (NS >= 16 || NS * R < 2) ? L : L + L / (PD * R);
 }
 
 // Load the R inputs of butterfly j of a pass from row `row` of `buf`.

@@ -30,7 +30,8 @@
 
 namespace ppf {
 
-template <int N_, int T_, class In_, int P_, int NT_, int RB_, int NCH_, int MINB_ = 1, class OT_ = float2>
+template <int N_, int T_, class In_, int P_, int NT_, int RB_, int NCH_, int MINB_ = 1, class OT_ = float2,
+          int NXB_ = 1>
 struct GatherCfg {
     using OT = OT_;  // output bin: float2 (complex64) or BinF16
     using In = In_;
@@ -38,6 +39,12 @@ struct GatherCfg {
     using coef_t = typename Coef<In>::type;
     static constexpr int N = N_, T = T_, P = P_, NT = NT_, RB = RB_, NCH = NCH_;
     static constexpr int MINB = MINB_;  // CTAs per SM the tile is built for
+    // FFT buffers per CTA: 1, or 2 (pipelined: round k+1 is filtered and sent
+    // into one buffer while round k is transformed in the other; the first
+    // pass's padding is halved, PD = 2, and the ring may be one chunk shorter
+    // so that both buffers fit)
+    static constexpr int NXB = NXB_;
+    static constexpr int PD = NXB_ == 2 ? 2 : 1;
     static constexpr int BPS = In::bytes;
     static constexpr int NC = N / P;                     // channels per CTA
     static constexpr int ROWS = P * RB;                  // spectra per round = input rows per ring chunk
@@ -50,15 +57,18 @@ struct GatherCfg {
     static constexpr int SEG_BYTES = NC * BPS;           // one input row's slice
     static constexpr int CHUNK_BYTES = ROWS * SEG_BYTES;
     static constexpr int RING_BYTES = NCH * CHUNK_BYTES;
-    static constexpr int RS = fft_row_stride(N);
-    static constexpr int X_SLOTS = RB * RS;              // the FFT buffer
-    static constexpr int XBYTES = RB * N * 8;            // bytes the buffer receives per round
-    static constexpr int SMEM = RING_BYTES + X_SLOTS * 8 + (NCH + 2) * 8;
+    static constexpr int RS = PD == 1 ? fft_row_stride(N) : N + (N / 32 > 2 ? N / 32 : 2);
+    static constexpr int X_SLOTS = RB * RS;              // one FFT buffer
+    static constexpr int XBYTES = RB * N * 8;            // bytes a buffer receives per round
+    static constexpr int SMEM = RING_BYTES + NXB * X_SLOTS * 8 + (NCH + 2 * NXB) * 8;
     static_assert(P >= 2 && P <= 8, "portable cluster sizes");
     static_assert(N % (2 * P) == 0 && SEG_BYTES % 16 == 0, "16-byte row slices");
     static_assert(UNITS % NT == 0 || NT % UNITS == 0, "FIR units must tile the threads");
     static_assert(ROWS % RG == 0 && RBT >= 1, "spectra per round must split over row groups");
-    static_assert(NCH >= KO + 2, "ring must hold a round's window plus one chunk in flight");
+    // one chunk in flight beyond the round's window; with two buffers the
+    // refill of a slot overlaps the FFT of the previous round instead
+    static_assert(NCH >= KO + 3 - NXB, "ring must hold a round's window plus one chunk in flight");
+    static_assert(NXB == 1 || NXB == 2, "one or two FFT buffers");
     static_assert(RS % 2 == 0, "16-byte aligned channel pairs in the FFT buffer");
     static_assert(XBYTES < (1 << 20), "mbarrier transaction count");
     static_assert(SMEM <= 232448, "shared memory per CTA");
@@ -76,10 +86,10 @@ ppf_gather_kernel(const PpfWork wl, const float2* __restrict__ tw, int* __restri
 
     extern __shared__ __align__(128) unsigned char smem[];
     unsigned char* ring = smem;
-    float2* X = reinterpret_cast<float2*>(smem + C::RING_BYTES);  // the FFT buffer
-    uint64_t* bars = reinterpret_cast<uint64_t*>(smem + C::RING_BYTES + C::X_SLOTS * 8);
-    uint64_t* xfull = bars + NCH;      // every byte of this CTA's buffer has arrived
-    uint64_t* xfree = bars + NCH + 1;  // every owner has finished reading its buffer
+    float2* X = reinterpret_cast<float2*>(smem + C::RING_BYTES);  // the FFT buffer(s)
+    uint64_t* bars = reinterpret_cast<uint64_t*>(smem + C::RING_BYTES + C::NXB * C::X_SLOTS * 8);
+    uint64_t* xfull = bars + NCH;            // [NXB] every byte of this CTA's buffer has arrived
+    uint64_t* xfree = bars + NCH + C::NXB;   // [NXB] every owner has finished reading its buffer
 
     const int tid = threadIdx.x;
     const int rank = (int)cluster_ctarank();
@@ -87,8 +97,10 @@ ppf_gather_kernel(const PpfWork wl, const float2* __restrict__ tw, int* __restri
 
     if (tid == 0) {
         for (int i = 0; i < NCH; ++i) mbar_init(&bars[i], 1);
-        mbar_init(xfull, 1);
-        mbar_init(xfree, P);
+        for (int b = 0; b < C::NXB; ++b) {
+            mbar_init(&xfull[b], 1);
+            mbar_init(&xfree[b], P);
+        }
         fence_mbar_init();
     }
     // every CTA of the cluster is running, with its mbarriers initialised,
@@ -185,9 +197,17 @@ ppf_gather_kernel(const PpfWork wl, const float2* __restrict__ tw, int* __restri
             }
         }
 
-        int waited = 0, rrb = (cbase % NCH) * ROWS;
-        for (int k = 0; k < nr; ++k) {
+        int waited = 0;
+        // Round k: its filtered rows go to FFT buffer b of every owner; with one
+        // buffer b = 0 and phase parities alternate per round, with two the
+        // rounds alternate between the buffers and each buffer's phases
+        // advance every second round.
+        auto buf_of = [&](int gk) { return C::NXB == 1 ? 0 : (gk & 1); };
+        auto phase_of = [&](int gk) { return (uint32_t)((C::NXB == 1 ? gk : (gk >> 1)) & 1); };
+        auto fir_round = [&](int k) {
             const int gk = gbase + k;
+            const int b = buf_of(gk);
+            const int rrb = ((cbase + k) % NCH) * ROWS;
             // 1. the round needs chunks k .. k+KO; every thread waits itself
             //    (a failure spreads over the CTA at the barrier after the FIR)
             const int need = (k + C::KO < nchunks ? k + C::KO : nchunks - 1) + 1;
@@ -198,11 +218,14 @@ ppf_gather_kernel(const PpfWork wl, const float2* __restrict__ tw, int* __restri
                     break;  // this chunk stays "not waited for": the drain below waits for it
                 }
             }
-            // every owner has finished reading its buffer in the previous round
-            // (each thread waits before its own stores into the buffers)
-            if (gk >= 1 && !failed && !mbar_wait_cluster_bounded(xfree, (uint32_t)((gk - 1) & 1))) failed = true;
-            if (tid == 0) mbar_arrive_expect_tx(xfull, (uint32_t)C::XBYTES);
-
+            // every owner has finished reading buffer b in the round that used it
+            // before (each thread waits before its own stores into the buffers;
+            // with two buffers only right before the stores, so the FIR overlaps it)
+            bool freed = C::NXB == 1 ? true : gk < 2;
+            if constexpr (C::NXB == 1) {
+                if (gk >= 1 && !failed && !mbar_wait_cluster_bounded(&xfree[0], phase_of(gk - 1))) failed = true;
+            }
+            if (tid == 0) mbar_arrive_expect_tx(&xfull[b], (uint32_t)C::XBYTES);
             // 2. FIR over the ring; row i of the round goes to CTA i / RB.
             //    With one row group the window starts at a chunk boundary:
             //    row u lies in the window's chunk u / ROWS at row u % ROWS, so
@@ -275,15 +298,19 @@ ppf_gather_kernel(const PpfWork wl, const float2* __restrict__ tw, int* __restri
                         }
                     }
                 }
+                if (!freed) {
+                    if (!failed && !mbar_wait_cluster_bounded(&xfree[b], phase_of(gk - 2))) failed = true;
+                    freed = true;
+                }
                 if (!failed) {
 #pragma unroll
                     for (int i = 0; i < RBT; ++i) {
                         const int row = i0 + i, q = row / RB, rr = row % RB;
                         const uint32_t off = (uint32_t)((rr * C::RS + rank * NC + cl) * 8);
                         if (PPF_INBOUNDS(off + 16 <= (uint32_t)C::X_SLOTS * 8 && q < P))
-                            st_async_f4(map_shared_rank(xbase + off, (uint32_t)q),
+                            st_async_f4(map_shared_rank(xbase + b * C::X_SLOTS * 8 + off, (uint32_t)q),
                                     make_float4(a0[i].x, a0[i].y, a1[i].x, a1[i].y),
-                                    map_shared_rank(fullbase, (uint32_t)q));
+                                    map_shared_rank(fullbase + b * 8, (uint32_t)q));
                     }
                 }
             }
@@ -293,18 +320,33 @@ ppf_gather_kernel(const PpfWork wl, const float2* __restrict__ tw, int* __restri
                 issue(issued);
                 ++issued;
             }
-            rrb += ROWS;
-            rrb = rrb >= RING_ROWS ? rrb - RING_ROWS : rrb;
-
+        };
+        auto fft_round = [&](int k) {
+            const int gk = gbase + k;
+            const int b = buf_of(gk);
             // 3. this CTA's block of the round: all N channels of its RB rows
-            if (!failed && !mbar_wait_bounded(xfull, (uint32_t)(gk & 1))) failed = true;
+            if (!failed && !mbar_wait_bounded(&xfull[b], phase_of(gk))) failed = true;
             const int64_t s0 = s_lo + (int64_t)k * ROWS + rank * RB;
             const int64_t left = s_hi - s0;
             const int rows = (int)(left < 0 ? 0 : (left < RB ? left : RB));
-            fft_rows_ip<N, RB, NT, 16, C::RS>(X, twr, Y + (rows > 0 ? s0 : 0) * N, rows, [&] {
+            fft_rows_ip<N, RB, NT, 16, C::RS, 0, C::PD>(X + b * C::X_SLOTS, twr, Y + (rows > 0 ? s0 : 0) * N,
+                                                        rows, [&] {
                 // 4. every thread's last read of the buffer is done: free it on every CTA
-                if (tid < P) mbar_arrive_cluster(map_shared_rank(freebase, (uint32_t)tid));
+                if (tid < P) mbar_arrive_cluster(map_shared_rank(freebase + b * 8, (uint32_t)tid));
             });
+        };
+        if constexpr (C::NXB == 1) {
+            for (int k = 0; k < nr; ++k) {
+                fir_round(k);
+                fft_round(k);
+            }
+        } else {
+            // round k+1 is filtered and sent while round k's rows arrive
+            if (nr > 0) fir_round(0);
+            for (int k = 0; k < nr; ++k) {
+                if (k + 1 < nr) fir_round(k + 1);
+                fft_round(k);
+            }
         }
         if (failed && tid == 0) {
             // let the copies still in flight land before the CTA moves on or exits

@@ -79,8 +79,8 @@ template <class C>
 KernelEntry entry()
 {
     static char name[80];
-    std::snprintf(name, sizeof(name), "gather:p%d:nt%d:rb%d:nch%d:b%d%s", C::P, C::NT, C::RB, C::NCH, C::MINB,
-                  std::is_same<typename C::OT, BinF16>::value ? ":f16" : "");
+    std::snprintf(name, sizeof(name), "gather:p%d:nt%d:rb%d:nch%d:b%d%s%s", C::P, C::NT, C::RB, C::NCH, C::MINB,
+                  C::NXB == 2 ? ":db" : "", std::is_same<typename C::OT, BinF16>::value ? ":f16" : "");
     KernelEntry e;
     e.name = name;
     e.prepare = prepare_gather<C>;
@@ -105,5 +105,18 @@ KernelEntry entry()
     if (N == NN && T == TT) {                                                                             \
         if (idx == want && out)                                                                           \
             *out = gather_detail::entry<GatherCfg<NN, TT, In, P, NT, RB, NCH, MINB, BinF16>>();           \
+        ++idx;                                                                                            \
+    }
+// PPF_GV2 / PPF_GVF2: the same with two FFT buffers per CTA (pipelined rounds).
+#define PPF_GV2(NN, TT, P, NT, RB, NCH, MINB)                                                             \
+    if (N == NN && T == TT) {                                                                             \
+        if (idx == want && out)                                                                           \
+            *out = gather_detail::entry<GatherCfg<NN, TT, In, P, NT, RB, NCH, MINB, float2, 2>>();        \
+        ++idx;                                                                                            \
+    }
+#define PPF_GVF2(NN, TT, P, NT, RB, NCH, MINB)                                                            \
+    if (N == NN && T == TT) {                                                                             \
+        if (idx == want && out)                                                                           \
+            *out = gather_detail::entry<GatherCfg<NN, TT, In, P, NT, RB, NCH, MINB, BinF16, 2>>();        \
         ++idx;                                                                                            \
     }

@@ -11,6 +11,8 @@ static int variants_impl(int N, int T, int want, KernelEntry* out)
     int idx = 0;
     PPF_GV(4096, 16, 4, 256, 1, 6, 1) PPF_GV(4096, 16, 4, 256, 2, 4, 1)
     PPF_GV(2048, 32, 4, 256, 2, 6, 1) PPF_GV(4096, 32, 8, 256, 1, 6, 1)
+    // two FFT buffers per CTA (pipelined rounds)
+    PPF_GV2(4096, 16, 4, 256, 1, 6, 1) PPF_GV2(2048, 32, 4, 256, 2, 6, 1) PPF_GV2(4096, 32, 8, 256, 1, 6, 1)
     return idx;
 }
 

@@ -131,7 +131,7 @@ __device__ __forceinline__ void fft_rows_pp(float2* a, float2* b, const PassTwid
 // the same rows (or, in the last pass, to global memory).  The barrier after
 // the last pass's loads also frees the buffer for the next block's FIR; the
 // caller's `after_last_read` runs right after it.
-template <int N, int RB, int NT, int R0, int RS, int P, class OT, class F>
+template <int N, int RB, int NT, int R0, int RS, int P, int PD, class OT, class F>
 __device__ __forceinline__ void fft_pass_ip(float2* buf, const PassTwiddlesR<N, NT, R0>& tw, OT* __restrict__ Yb,
                                             int rows, F&& after_last_read)
 {
@@ -149,10 +149,10 @@ __device__ __forceinline__ void fft_pass_ip(float2* buf, const PassTwiddlesR<N, 
         const int b = threadIdx.x + k * NT;
         if (NB % NT == 0 || b < NB) {
             const int row = b / BPR, j = b % BPR;
-            const int bx = row * RS + (IN_NS == 0 ? j : pad_slot<IN_NS, IN_R>(j));
+            const int bx = row * RS + (IN_NS == 0 ? j : pad_slot<IN_NS, IN_R, PD>(j));
 #pragma unroll
             for (int r = 0; r < R; ++r) {
-                const int ix = bx + r * (IN_NS == 0 ? N / R : pad_stride<IN_NS, IN_R, N / R>());
+                const int ix = bx + r * (IN_NS == 0 ? N / R : pad_stride<IN_NS, IN_R, N / R, PD>());
                 v[k][r] = PPF_INBOUNDS(ix < RB * RS) ? buf[ix] : make_float2(0.f, 0.f);
             }
         }
@@ -174,7 +174,7 @@ __device__ __forceinline__ void fft_pass_ip(float2* buf, const PassTwiddlesR<N, 
                         if (PPF_INBOUNDS(j + q * NS < N)) st_bin(o + q * NS, v[k][q]);
                 }
             } else {
-                const int ox = row * RS + pad_slot<NS, R>((j / NS) * NS * R + (j % NS));
+                const int ox = row * RS + pad_slot<NS, R, PD>((j / NS) * NS * R + (j % NS));
 #pragma unroll
                 for (int q = 0; q < R; ++q)
                     if (PPF_INBOUNDS(ox + q * NS < RB * RS)) buf[ox + q * NS] = v[k][q];
@@ -184,13 +184,13 @@ __device__ __forceinline__ void fft_pass_ip(float2* buf, const PassTwiddlesR<N, 
     if constexpr (!LAST) __syncthreads();
 }
 
-template <int N, int RB, int NT, int R0, int RS, int P = 0, class OT, class F>
+template <int N, int RB, int NT, int R0, int RS, int P = 0, int PD = 1, class OT, class F>
 __device__ __forceinline__ void fft_rows_ip(float2* buf, const PassTwiddlesR<N, NT, R0>& tw, OT* __restrict__ Yb,
                                             int rows, F&& after_last_read)
 {
     if constexpr (P < fft_npass_r(N, R0)) {
-        fft_pass_ip<N, RB, NT, R0, RS, P>(buf, tw, Yb, rows, after_last_read);
-        fft_rows_ip<N, RB, NT, R0, RS, P + 1>(buf, tw, Yb, rows, after_last_read);
+        fft_pass_ip<N, RB, NT, R0, RS, P, PD>(buf, tw, Yb, rows, after_last_read);
+        fft_rows_ip<N, RB, NT, R0, RS, P + 1, PD>(buf, tw, Yb, rows, after_last_read);
     }
 }
 
