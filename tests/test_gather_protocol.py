@@ -1,0 +1,141 @@
+"""Model of the gather kernel's pipelined round protocol (two FFT buffers per CTA).
+
+The kernel (paper_1411_3656_gb300/csrc/ppf_gather.cuh, tiles named ":db") runs, on
+each of the P CTAs of a cluster: FIR of round 0; then for every round k, the FIR of
+round k+1 and the FFT of round k.  Round g uses FFT buffer b = g mod 2 of every owner;
+each buffer has a "full" mbarrier (one local arrival with the expected bytes, plus the
+P slices other CTAs store into it, counted as transaction bytes) and a "free"
+mbarrier (P arrivals, one per owner after its last FFT-pass loads of that buffer).
+A sender waits for phase (g-2)/2 of its own "free" barrier of buffer b before
+storing round g; an owner waits for phase g/2 of its "full" barrier before
+transforming round g.  Waits use the parity of the phase, so the model also checks
+that no barrier is ever more than one phase ahead of the phase waited for.
+
+Random interleavings of the CTAs must never deadlock, never let a slice of round g
+land in a buffer an owner still reads for round g-2, and give every FFT exactly the P
+slices of its own round.  Host-only: no GPU.
+"""
+import random
+
+import pytest
+
+
+class Barrier:
+    """An mbarrier phase counter: a phase completes after `count` arrivals and,
+    for the 'full' barriers, `tx` transaction units."""
+
+    def __init__(self, count, tx=0):
+        self.count, self.tx_needed = count, tx
+        self.completed = 0
+        self.arrivals = 0
+        self.tx = 0
+
+    def _maybe_complete(self):
+        if self.arrivals == self.count and self.tx == self.tx_needed:
+            self.completed += 1
+            self.arrivals = 0
+            self.tx = 0
+
+    def arrive(self):
+        self.arrivals += 1
+        assert self.arrivals <= self.count
+        self._maybe_complete()
+
+    def complete_tx(self):
+        self.tx += 1
+        assert self.tx <= self.tx_needed
+        self._maybe_complete()
+
+    def wait_ready(self, phase):
+        # parity wait for phase `phase`: true once that phase has completed; the
+        # barrier must not have run a further phase (its parity would match again)
+        assert self.completed <= phase + 1, "barrier ran two phases ahead of a waiter"
+        return self.completed == phase + 1
+
+
+class CTA:
+    def __init__(self, rank, P):
+        self.rank, self.P = rank, P
+        self.full = [Barrier(1, P), Barrier(1, P)]
+        self.free = [Barrier(P), Barrier(P), ]
+        self.buf = [dict(), dict()]      # buffer b: {sender rank: round}
+        self.reading = [None, None]      # round being transformed in buffer b
+        self.done_rounds = []
+
+
+def cta_program(me, ctas, nr):
+    P = len(ctas)
+
+    def fir(g):
+        b = g & 1
+        # the local arrival with the expected bytes belongs to phase g/2
+        assert me.full[b].completed == g >> 1
+        me.full[b].arrive()
+        yield None  # the FIR arithmetic
+        if g >= 2:
+            while not me.free[b].wait_ready((g - 2) >> 1):
+                yield "wait"
+        for owner in ctas:
+            # the owner may not still be reading round g-2 from this buffer
+            assert owner.reading[b] != g - 2, "slice stored into a buffer still being read"
+            assert owner.full[b].completed == g >> 1
+            owner.buf[b][me.rank] = g
+            owner.full[b].complete_tx()
+            yield None
+
+    def fft(g):
+        b = g & 1
+        while not me.full[b].wait_ready(g >> 1):
+            yield "wait"
+        assert me.buf[b] == {r: g for r in range(P)}, "FFT input is not exactly round g's slices"
+        me.reading[b] = g
+        yield None  # the passes' loads
+        me.reading[b] = None
+        for peer in ctas:
+            peer.free[b].arrive()
+        yield None  # the rest of the passes and the stores
+        me.done_rounds.append(g)
+
+    if nr > 0:
+        yield from fir(0)
+    for k in range(nr):
+        if k + 1 < nr:
+            yield from fir(k + 1)
+        yield from fft(k)
+
+
+@pytest.mark.parametrize("P,nr,seed", [(2, 1, 0), (2, 2, 1), (2, 9, 2), (4, 7, 3), (8, 12, 4), (8, 3, 5), (3, 10, 6)])
+def test_pipelined_rounds_complete_without_overwrites(P, nr, seed):
+    rng = random.Random(seed)
+    for trial in range(40):
+        ctas = [CTA(r, P) for r in range(P)]
+        progs = {r: cta_program(ctas[r], ctas, nr) for r in range(P)}
+        blocked = {r: False for r in range(P)}
+        live = set(range(P))
+        steps = 0
+        while live:
+            steps += 1
+            assert steps < 100000
+            r = rng.choice(sorted(live))
+            try:
+                st = next(progs[r])
+            except StopIteration:
+                live.discard(r)
+                continue
+            blocked[r] = st == "wait"
+            if live and all(blocked[q] for q in live):
+                # every live CTA is waiting: one more round of polls must free one
+                progressed = False
+                for q in sorted(live):
+                    try:
+                        st = next(progs[q])
+                    except StopIteration:
+                        live.discard(q)
+                        progressed = True
+                        continue
+                    if st != "wait":
+                        blocked[q] = False
+                        progressed = True
+                assert progressed or not live, f"deadlock (P={P}, rounds={nr}, trial={trial})"
+        for c in ctas:
+            assert c.done_rounds == list(range(nr))
