@@ -71,3 +71,21 @@ def test_stream_state_and_checker_entry_points_without_a_device(lib):
     out = ctypes.c_void_p()
     assert lib.ppf_stream_restore(None, buf, 64, ctypes.byref(out), None) == 1
     assert lib.ppf_check_violations(0) == -1
+
+
+def test_tuned_table_names_compiled_variants(lib):
+    """Every entry of the autotuned table (csrc/ppf_tuned.inc) names the compiled
+    variant at its index (a stale entry would silently fall back to variant 0)."""
+    import re
+    from paper_1411_3656_gb300 import ppf
+    path = os.path.join(ROOT, "paper_1411_3656_gb300", "csrc", "ppf_tuned.inc")
+    dtypes = {v: k for k, v in ppf.DTYPES.items()}
+    n = 0
+    for ln in open(path):
+        m = re.match(r'PPF_TUNED\((\d+), (\d+), (\d+), (\d+), "([^"]+)"\)', ln)
+        if not m:
+            continue
+        N, T, d, i, name = int(m[1]), int(m[2]), int(m[3]), int(m[4]), m[5]
+        assert ppf.ppf_variant_name(N, T, dtypes[d], i) == name, ln
+        n += 1
+    assert n >= 3 * 20
