@@ -20,8 +20,8 @@
  * PPF_ERR_CUDA.
  *
  * Conventions shared by all entry points:
- *   - Sizes: N is a power of two, 4 <= N <= 4096; 1 <= T <= 64.  Anything
- *     else is PPF_ERR_UNSUPPORTED.  int8 input needs N >= 8.
+ *   - Sizes: N is a power of two, 4 <= N <= 4096; 1 <= T <= 64, for every
+ *     input type.  Anything else is PPF_ERR_UNSUPPORTED.
  *   - Samples: PPF_IN_C32 = float2 (I, Q) 8 bytes; PPF_IN_C16 = two IEEE
  *     half values (I, Q) 4 bytes; PPF_IN_CI8 = two signed 8-bit integers
  *     (I, Q) 2 bytes, used unscaled.  Output is float2 (complex64), or FP16
@@ -35,10 +35,8 @@
  *     waiting.  Argument errors are reported synchronously and enqueue
  *     nothing.  Errors of earlier asynchronous work surface as PPF_ERR_CUDA.
  *   - A plan is immutable after creation and may be used from several host
- *     threads at once.  Executions of one plan on different CUDA streams must
- *     be ordered when its kernel uses plan-owned scratch (the cooperative
- *     split kernel for large N*T, see ppf_plan_kernel_name "split:..."); use
- *     one plan per stream otherwise.  A stream object is not thread-safe.
+ *     threads and CUDA streams at once (its kernels keep no state in device
+ *     memory between launches).  A stream object is not thread-safe.
  */
 #ifndef PPF_H_
 #define PPF_H_
@@ -157,6 +155,9 @@ ppf_status_t ppf_stream_open(ppf_plan_t plan, ppf_stream_t* out);
  *                         stream is unchanged.
  *   n_spectra_out [out]   spectra written by this push.
  * Ordered on `stream`; the history update is enqueued on the same stream.
+ * Successive pushes of one stream object may use different CUDA streams: a
+ * push made on another stream than the previous one first makes its stream
+ * wait (an event) for the work the previous push enqueued.
  */
 ppf_status_t ppf_stream_push(ppf_stream_t s, const void* d_chunk, int64_t n_samples,
                              void* d_out, int64_t out_capacity_spectra,
@@ -192,16 +193,16 @@ ppf_status_t ppf_stream_restore(ppf_plan_t plan, const void* h_state, size_t byt
 /*
  * ppf_execute_noalloc -- the whole PPF with no plan and no device allocation.
  * The paper has no counterpart; this is for callers that cannot allocate
- * device memory when they need a filter bank: code running while a stream is
- * captured into a CUDA graph (cudaMalloc is not allowed there), plug-ins whose
- * host framework owns all device memory and forbids cudaMalloc/cudaFree, and
- * real-time threads that must not block on the allocator's device-wide
- * synchronisation.
+ * device memory when they need a filter bank: plug-ins whose host framework
+ * owns all device memory and forbids cudaMalloc/cudaFree, and real-time
+ * threads that must not block on the allocator (cudaMalloc and cudaFree can
+ * synchronise the whole device).
  *   N, T, dtype  as for ppf_plan_create; N at most 4096 (the scratch limit:
  *                larger N returns PPF_ERR_UNSUPPORTED).
  *   d_h          device array of N*T float coefficients, h[t*N + c] (FP32 for
  *                every input type).  Read only.
- *   d_in, d_out, n_spectra, stream  as for ppf_execute.
+ *   d_in, d_out, n_spectra, stream  as for ppf_execute.  d_h must not overlap
+ *                d_out either (PPF_ERR_MISALIGNED).
  * Runs the general fused kernel.  Its FFT twiddle table is scratch kept in one
  * library-wide static device array of 4096 complex values (32 KiB per GPU
  * that loads the library, held until exit), rewritten by every call on the
@@ -209,7 +210,9 @@ ppf_status_t ppf_stream_restore(ppf_plan_t plan, const void* h_state, size_t byt
  * same stream from several threads without ordering) share that array and
  * race.  The first call on each device runs a one-time set-up (symbol
  * address, kernel attributes); make that first call before any stream capture
- * begins.  Allocates nothing, frees nothing, calls no allocating library.
+ * begins.  A set-up that fails returns PPF_ERR_CUDA and is tried again by the
+ * next call; only a successful one is kept.  Allocates nothing, frees
+ * nothing, calls no allocating library.
  */
 ppf_status_t ppf_execute_noalloc(int N, int T, ppf_dtype_t dtype, const float* d_h, const void* d_in,
                                  void* d_out, int64_t n_spectra, void* stream);

@@ -39,7 +39,6 @@ struct ppf_plan_s {
     void* d_h = nullptr;
     float2* d_tw = nullptr;
     int* h_err = nullptr;    // mapped host word a kernel sets when a bounded wait gives up
-    void* d_scratch = nullptr;  // kernel scratch (split kernel: group counters and exchange rows)
     // staging for ppf_execute_host (allocated on first use)
     std::mutex host_mu;
     void* d_stage_in[2] = {nullptr, nullptr};
@@ -58,6 +57,8 @@ struct ppf_stream_s {
     int64_t pushed = 0;                   // total samples pushed
     int64_t emitted = 0;                  // total spectra emitted
     cudaStream_t last = nullptr;          // CUDA stream of the last push
+    bool has_last = false;                // a push (or restore) has enqueued work on `last`
+    cudaEvent_t order_ev = nullptr;       // orders a push after the previous one on another stream
 };
 
 namespace {
@@ -113,7 +114,6 @@ void free_plan_memory(ppf_plan_s* p)
     if (p->d_h) cudaFree(p->d_h);
     if (p->d_tw) cudaFree(p->d_tw);
     if (p->h_err) cudaFreeHost(p->h_err);
-    if (p->d_scratch) cudaFree(p->d_scratch);
     for (int i = 0; i < 2; ++i) {
         if (p->d_stage_in[i]) cudaFree(p->d_stage_in[i]);
         if (p->d_stage_out[i]) cudaFree(p->d_stage_out[i]);
@@ -156,7 +156,6 @@ ppf_status_t ppf_plan_create(ppf_plan_t* out, int N, int T, const float* h_host,
     const int bps = sample_bytes(in_dtype);
     if (bps == 0) return PPF_ERR_UNSUPPORTED;
     if (!is_pow2(N) || N < 4 || N > 4096 || T < 1 || T > 64) return PPF_ERR_UNSUPPORTED;
-    if (in_dtype == PPF_IN_CI8 && N < 8) return PPF_ERR_UNSUPPORTED;
     if (flags & ~(PPF_FLAG_FIR_ONLY | PPF_FLAG_GENERIC | PPF_FLAG_OUT_F16 | 0xFF00u)) return PPF_ERR_INVALID_ARG;
     if ((flags & PPF_FLAG_FIR_ONLY) && (flags & PPF_FLAG_OUT_F16)) return PPF_ERR_UNSUPPORTED;
     const int variant = (int)((flags >> 8) & 0xFFu) - 1;  // -1: tuned default
@@ -233,11 +232,6 @@ ppf_status_t ppf_plan_create(ppf_plan_t* out, int N, int T, const float* h_host,
     }
     e = p->entry.prepare(p->view);
     if (e == cudaSuccess) e = p->fir_entry.prepare(p->fir_view);
-    if (e == cudaSuccess && p->view.scratch_bytes > 0) {
-        e = cudaMalloc(&p->d_scratch, p->view.scratch_bytes);
-        if (e == cudaSuccess) e = cudaMemset(p->d_scratch, 0, p->view.scratch_bytes);
-        p->view.scratch = p->d_scratch;
-    }
     if (e != cudaSuccess) {
         free_plan_memory(p);
         delete p;
@@ -380,6 +374,16 @@ ppf_status_t ppf_stream_push(ppf_stream_t s, const void* d_chunk, int64_t n_samp
     cudaStream_t st = static_cast<cudaStream_t>(stream);
     cudaError_t e = cudaSuccess;
 
+    // Pushes of one stream object may come on different CUDA streams: this
+    // push's copies, kernel and frees are ordered after everything the
+    // previous push enqueued on its own stream.
+    if (s->has_last && st != s->last) {
+        if (!s->order_ev) e = cudaEventCreateWithFlags(&s->order_ev, cudaEventDisableTiming);
+        if (e == cudaSuccess) e = cudaEventRecord(s->order_ev, s->last);
+        if (e == cudaSuccess) e = cudaStreamWaitEvent(st, s->order_ev, 0);
+        if (e != cudaSuccess) return from_cuda(e);
+    }
+
     // Grow the two buffers so they hold the history plus this chunk.
     const int64_t need = s->held + n_samples;
     if (need > s->cap) {
@@ -409,6 +413,7 @@ ppf_status_t ppf_stream_push(ppf_stream_t s, const void* d_chunk, int64_t n_samp
     s->held += n_samples;
     s->pushed = total;
     s->last = st;
+    s->has_last = true;
     if (fresh > 0) {
         // The live buffer always starts at the first row of spectrum s->emitted.
         e = plan->entry.launch(plan->view, buf, static_cast<float2*>(d_out), fresh, st);
@@ -455,8 +460,9 @@ ppf_status_t ppf_stream_save(ppf_stream_t s, void* h_state, size_t capacity_byte
     const size_t need = sizeof(StreamStateHeader) + (size_t)s->held * bps;
     if (capacity_bytes < need) return PPF_ERR_INVALID_ARG;
     if (pending_cuda_error()) return PPF_ERR_CUDA;
-    // the pushes enqueued so far must have written the history
-    cudaError_t e = s->last ? cudaStreamSynchronize(s->last) : cudaSuccess;
+    // the pushes enqueued so far must have written the history (every push
+    // is ordered after the one before, so the last push's stream covers all)
+    cudaError_t e = s->has_last ? cudaStreamSynchronize(s->last) : cudaSuccess;
     if (e != cudaSuccess) return from_cuda(e);
     StreamStateHeader hd{};
     std::memcpy(hd.magic, "PPFS", 4);
@@ -521,6 +527,7 @@ ppf_status_t ppf_stream_restore(ppf_plan_t plan, const void* h_state, size_t byt
     s->emitted = hd.emitted;
     s->base = hd.emitted * N;
     s->last = st;
+    s->has_last = true;
     *out = s;
     return PPF_OK;
 }
@@ -536,6 +543,7 @@ ppf_status_t ppf_stream_close(ppf_stream_t s)
         }
     cudaError_t e2 = s->last ? cudaStreamSynchronize(s->last) : cudaDeviceSynchronize();
     if (e == cudaSuccess) e = e2;
+    if (s->order_ev) cudaEventDestroy(s->order_ev);
     delete s;
     return from_cuda(e);
 }

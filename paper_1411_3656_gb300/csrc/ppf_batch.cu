@@ -121,7 +121,6 @@ ppf_status_t ppf_batch_create(ppf_batch_t* out, const ppf_job_t* jobs, int n_job
     struct Layout {
         std::vector<ppf::PpfJob> jobs;
         std::vector<ppf::PpfItem> items;
-        std::vector<std::vector<unsigned char>> maps;  // 128-byte tensor maps
     };
     std::vector<Layout> lay(order.size());
     size_t bytes = 0;
@@ -145,14 +144,6 @@ ppf_status_t ppf_batch_create(ppf_batch_t* out, const ppf_job_t* jobs, int n_job
             pj.h = v.h;
             pj.S = j.n_spectra;
             const int jid = (int)L.jobs.size();
-            if (pg.entry.encode) {
-                std::vector<unsigned char> m(128, 0);
-                if (!pg.entry.encode(m.data(), j.d_in, j.n_spectra + v.T - 1)) {
-                    delete b;
-                    return PPF_ERR_INVALID_ARG;
-                }
-                L.maps.push_back(std::move(m));
-            }
             L.jobs.push_back(pj);
             const int64_t nblk = (j.n_spectra + RB - 1) / RB;
             const int64_t pieces = std::max<int64_t>(1, (nblk + target / 2) / target);
@@ -164,7 +155,7 @@ ppf_status_t ppf_batch_create(ppf_batch_t* out, const ppf_job_t* jobs, int n_job
                 if (it.bhi > it.blo) L.items.push_back(it);
             }
         }
-        bytes += 128 * L.maps.size() + sizeof(ppf::PpfJob) * L.jobs.size() + sizeof(ppf::PpfItem) * L.items.size() + 384;
+        bytes += sizeof(ppf::PpfJob) * L.jobs.size() + sizeof(ppf::PpfItem) * L.items.size() + 256;
     }
 
     // 3. one device allocation for every table
@@ -186,11 +177,6 @@ ppf_status_t ppf_batch_create(ppf_batch_t* out, const ppf_job_t* jobs, int n_job
     for (size_t gi = 0; gi < order.size(); ++gi) {
         Pending& pg = by_kernel[order[gi]];
         Layout& L = lay[gi];
-        const size_t maps_at = place(128 * L.maps.size(), 128);
-        for (size_t k = 0; k < L.maps.size(); ++k) {
-            std::memcpy(&host[maps_at + 128 * k], L.maps[k].data(), 128);
-            L.jobs[k].tmap = static_cast<unsigned char*>(b->dev) + maps_at + 128 * k;
-        }
         const size_t jobs_at = place(sizeof(ppf::PpfJob) * L.jobs.size(), 16);
         std::memcpy(&host[jobs_at], L.jobs.data(), sizeof(ppf::PpfJob) * L.jobs.size());
         const size_t items_at = place(sizeof(ppf::PpfItem) * L.items.size(), 16);

@@ -210,24 +210,6 @@ template <> struct Pair<InCI8> {
     }
 };
 
-// The same decodes with int8 converted by the conversion instruction, which
-// runs on its own (quarter-rate) pipe: the better choice where the FP32 pipe
-// is the tighter resource (the four-step cluster kernel at large T measured
-// 10% slower with the byte-permute form).  Values are identical either way.
-template <class In>
-__device__ __forceinline__ void split_cvt(const typename Pair<In>::vec& p, float2& a, float2& b)
-{
-    if constexpr (std::is_same<In, InCI8>::value) {
-        a = make_float2((float)p.x, (float)p.y);
-        b = make_float2((float)p.z, (float)p.w);
-    } else {
-        Pair<In>::split(p, a, b);
-    }
-}
-__device__ __forceinline__ float2 decode_cvt(char2 v) { return make_float2((float)v.x, (float)v.y); }
-template <class R>
-__device__ __forceinline__ float2 decode_cvt(R v) { return decode(v); }
-
 // One FIR tap of a channel pair stored as FP16: h = (h0, h1) and the samples
 // x = ((re0, im0), (re1, im1)) as FP16 pairs; a0 += h0 * x0, a1 += h1 * x1 per
 // component with the mixed-precision FMA (FP16 operands, FP32 accumulator:
@@ -285,12 +267,10 @@ __device__ __forceinline__ void st_bin(BinF16* p, float2 v)
 // ------------------------------------------------------------------ work lists
 // One job of a launch: a contiguous input stream (S + T - 1 rows of N samples),
 // its S output spectra and its coefficients (each stream may have its own h).
-// `tmap` is the job's input tensor map in global memory (cluster kernel only).
 struct PpfJob {
     const void* x;
     float2* Y;
     const void* h;
-    const void* tmap;
     int64_t S;
 };
 // A work item: blocks [blo, bhi) of job `job` (a block is the kernel's RB spectra).

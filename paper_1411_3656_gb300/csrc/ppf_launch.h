@@ -18,8 +18,6 @@ struct PlanView {
     int fir_only = 0;             // test hook: store y instead of Y
     int out_f16 = 0;              // output bins are FP16 (I, Q) pairs instead of complex64
     int* err = nullptr;           // device-visible error word (mapped host memory)
-    void* scratch = nullptr;      // plan-owned device scratch (split kernel: counters + exchange rows)
-    size_t scratch_bytes = 0;     // set by prepare; the plan allocates it
 };
 
 using PrepareFn = cudaError_t (*)(PlanView&);
@@ -28,15 +26,12 @@ using LaunchFn = cudaError_t (*)(const PlanView&, const void* in, float2* out, i
 // One launch over a device work list (items/jobs in device memory); `grid`
 // CTAs (a multiple of the cluster size).
 using LaunchWorkFn = cudaError_t (*)(const PlanView&, const PpfWork& work, int grid, cudaStream_t stream);
-// Encode a job's input tensor map (cluster kernels); 128 bytes.
-using EncodeFn = bool (*)(void* tmap128, const void* x, int64_t rows);
 
 struct KernelEntry {
     const char* name = nullptr;
     PrepareFn prepare = nullptr;
     LaunchFn launch = nullptr;
     LaunchWorkFn launch_work = nullptr;  // null: no work-list form (general kernel)
-    EncodeFn encode = nullptr;           // null: jobs need no tensor map
     int rows_per_block = 0;              // spectra per block (RB)
     int cluster = 1;                     // CTAs per cluster
 };

@@ -1,13 +1,12 @@
 // ppf_execute_noalloc: the whole PPF without any device allocation.
 //
 // Some callers cannot allocate device memory at the point where they need a
-// filter bank: code running while a CUDA stream is being captured into a graph
-// (cudaMalloc is not allowed there), plug-ins hosted by a framework that owns
-// all device memory and forbids direct cudaMalloc/cudaFree, and real-time
-// threads that must not block on the allocator's device-wide synchronisation.
-// For them this entry point runs the general fused kernel with no plan: the
-// caller passes the coefficients as a device array, and the one piece of
-// scratch memory the kernel needs, the FFT twiddle table, lives in a
+// filter bank: plug-ins hosted by a framework that owns all device memory and
+// forbids direct cudaMalloc/cudaFree, and real-time threads that must not
+// block on the allocator (cudaMalloc and cudaFree can synchronise the whole
+// device).  For them this entry point runs the general fused kernel with no
+// plan: the caller passes the coefficients as a device array, and the one
+// piece of scratch memory the kernel needs, the FFT twiddle table, lives in a
 // file-scope __device__ array of at most 4096 complex values (32 KiB, held by
 // every GPU that loads the library until the process exits).
 #include "ppf.h"
@@ -16,6 +15,7 @@
 
 #include <cuda_runtime.h>
 
+#include <atomic>
 #include <cstdint>
 #include <mutex>
 
@@ -29,8 +29,8 @@ constexpr int kMaxDevices = 64;
 static __device__ __align__(256) float2 g_noalloc_twiddles[kNoallocMaxN];
 
 struct DeviceSetup {
-    std::once_flag once;
-    cudaError_t err = cudaSuccess;
+    std::mutex mu;
+    std::atomic<bool> ready{false};  // set only once a set-up has succeeded
     float2* tw = nullptr;  // device address of g_noalloc_twiddles on this device
     int sms = 0;
     int occ[3][13] = {};   // resident CTAs per SM of the general kernel, [dtype][log2 N]
@@ -67,7 +67,7 @@ template <class In>
 cudaError_t setup_dtype(DeviceSetup& d, int dt)
 {
     cudaError_t e = cudaSuccess;
-    if (e == cudaSuccess && dt != 2) e = setup_one<4, In>(d, dt);
+    if (e == cudaSuccess) e = setup_one<4, In>(d, dt);
     if (e == cudaSuccess) e = setup_one<8, In>(d, dt);
     if (e == cudaSuccess) e = setup_one<16, In>(d, dt);
     if (e == cudaSuccess) e = setup_one<32, In>(d, dt);
@@ -82,15 +82,23 @@ cudaError_t setup_dtype(DeviceSetup& d, int dt)
 }
 
 // Once per device, with that device current: the scratch's device address,
-// kernel attributes and occupancy.  Allocates nothing.
-void setup_device(DeviceSetup& d, int dev)
+// kernel attributes and occupancy.  Allocates nothing.  Only success is
+// remembered: a set-up that fails (its error is returned, and cleared from
+// CUDA's last-error state unless the context itself is broken) is tried
+// again by the next call.
+cudaError_t ensure_setup(DeviceSetup& d, int dev)
 {
+    if (d.ready.load(std::memory_order_acquire)) return cudaSuccess;
+    std::lock_guard<std::mutex> lock(d.mu);
+    if (d.ready.load(std::memory_order_relaxed)) return cudaSuccess;
     cudaError_t e = cudaGetSymbolAddress(reinterpret_cast<void**>(&d.tw), g_noalloc_twiddles);
     if (e == cudaSuccess) e = cudaDeviceGetAttribute(&d.sms, cudaDevAttrMultiProcessorCount, dev);
     if (e == cudaSuccess) e = setup_dtype<ppf::InC32>(d, 0);
     if (e == cudaSuccess) e = setup_dtype<ppf::InC16>(d, 1);
     if (e == cudaSuccess) e = setup_dtype<ppf::InCI8>(d, 2);
-    d.err = e;
+    if (e == cudaSuccess) d.ready.store(true, std::memory_order_release);
+    else cudaGetLastError();
+    return e;
 }
 
 template <int N, class In>
@@ -140,21 +148,21 @@ extern "C" ppf_status_t ppf_execute_noalloc(int N, int T, ppf_dtype_t dtype, con
     if (bps == 0) return PPF_ERR_UNSUPPORTED;
     // N above kNoallocMaxN would not fit the twiddle scratch.
     if (N < 4 || N > kNoallocMaxN || (N & (N - 1)) != 0 || T < 1 || T > 64) return PPF_ERR_UNSUPPORTED;
-    if (dtype == PPF_IN_CI8 && N < 8) return PPF_ERR_UNSUPPORTED;
     if (n_spectra < 0) return PPF_ERR_INVALID_ARG;
     if (n_spectra == 0) return PPF_OK;
     if (!d_h || !d_in || !d_out) return PPF_ERR_INVALID_ARG;
     if (!aligned16(d_in) || !aligned16(d_out)) return PPF_ERR_MISALIGNED;
     const uintptr_t i0 = reinterpret_cast<uintptr_t>(d_in), o0 = reinterpret_cast<uintptr_t>(d_out);
     const uintptr_t in_bytes = (uintptr_t)(n_spectra + T - 1) * N * bps, out_bytes = (uintptr_t)n_spectra * N * 8;
+    const uintptr_t h0 = reinterpret_cast<uintptr_t>(d_h), h_bytes = (uintptr_t)N * T * sizeof(float);
     if (i0 < o0 + out_bytes && o0 < i0 + in_bytes) return PPF_ERR_MISALIGNED;
+    if (h0 < o0 + out_bytes && o0 < h0 + h_bytes) return PPF_ERR_MISALIGNED;
     if (cudaPeekAtLastError() != cudaSuccess) return PPF_ERR_CUDA;
     int dev = 0;
     if (cudaGetDevice(&dev) != cudaSuccess) return PPF_ERR_CUDA;
     if (dev < 0 || dev >= kMaxDevices) return PPF_ERR_UNSUPPORTED;
     DeviceSetup& d = g_setup[dev];
-    std::call_once(d.once, [&] { setup_device(d, dev); });
-    if (d.err != cudaSuccess) return PPF_ERR_CUDA;
+    if (ensure_setup(d, dev) != cudaSuccess) return PPF_ERR_CUDA;
 
     cudaStream_t st = static_cast<cudaStream_t>(stream);
     fill_noalloc_twiddles<<<(N + 255) / 256, 256, 0, st>>>(d.tw, N);

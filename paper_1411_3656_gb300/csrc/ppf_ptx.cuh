@@ -83,46 +83,6 @@ __device__ __forceinline__ void tma_load_1d(void* dst, const void* src, uint32_t
         : "memory");
 }
 
-// 3-D tiled copy global -> this CTA's shared memory (tensor map in param space).
-__device__ __forceinline__ void tma_load_3d(void* dst, const void* tmap, int c0, int c1, int c2, uint64_t* bar,
-                                            uint64_t policy)
-{
-    asm volatile(
-        "cp.async.bulk.tensor.3d.shared::cluster.global.tile.mbarrier::complete_tx::bytes.L2::cache_hint"
-        " [%0], [%1, {%2, %3, %4}], [%5], %6;" ::"r"(smem_u32(dst)),
-        "l"(tmap), "r"(c0), "r"(c1), "r"(c2), "r"(smem_u32(bar)), "l"(policy)
-        : "memory");
-}
-
-// 3-D tiled copy this CTA's shared memory -> global (bulk-group completion).
-__device__ __forceinline__ void tma_store_3d(const void* tmap, const void* src, int c0, int c1, int c2)
-{
-    asm volatile("cp.async.bulk.tensor.3d.global.shared::cta.tile.bulk_group [%0, {%2, %3, %4}], [%1];" ::"l"(tmap),
-                 "r"(smem_u32(src)), "r"(c0), "r"(c1), "r"(c2)
-                 : "memory");
-}
-
-__device__ __forceinline__ void bulk_commit() { asm volatile("cp.async.bulk.commit_group;" ::: "memory"); }
-
-// Wait until at most N bulk groups of this thread are still reading shared memory.
-template <int N>
-__device__ __forceinline__ void bulk_wait_read()
-{
-    asm volatile("cp.async.bulk.wait_group.read %0;" ::"n"(N) : "memory");
-}
-
-template <int N>
-__device__ __forceinline__ void bulk_wait()
-{
-    asm volatile("cp.async.bulk.wait_group %0;" ::"n"(N) : "memory");
-}
-
-// Order this thread's generic-proxy shared-memory writes before later async-proxy reads.
-__device__ __forceinline__ void fence_proxy_async_smem()
-{
-    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-}
-
 // ---------------------------------------------------------------- clusters
 __device__ __forceinline__ uint32_t cluster_ctarank()
 {
@@ -149,29 +109,10 @@ __device__ __forceinline__ uint32_t map_shared_rank(uint32_t addr, uint32_t rank
     return r;
 }
 
-__device__ __forceinline__ void st_cluster_f2(uint32_t addr, float2 v)
-{
-    asm volatile("st.shared::cluster.v2.f32 [%0], {%1, %2};" ::"r"(addr), "f"(v.x), "f"(v.y) : "memory");
-}
-
-__device__ __forceinline__ void st_cluster_f4(uint32_t addr, float4 v)
-{
-    asm volatile("st.shared::cluster.v4.f32 [%0], {%1, %2, %3, %4};" ::"r"(addr), "f"(v.x), "f"(v.y), "f"(v.z),
-                 "f"(v.w)
-                 : "memory");
-}
-
-// Asynchronous store of 8 bytes into a peer CTA's shared memory; completion is
-// counted (8 bytes of complete_tx) on the peer's mbarrier `rbar`.  No fence is
-// needed: the receiver observes the data through that mbarrier.
-__device__ __forceinline__ void st_async_f2(uint32_t addr, float2 v, uint32_t rbar)
-{
-    asm volatile("st.async.shared::cluster.mbarrier::complete_tx::bytes.v2.f32 [%0], {%1, %2}, [%3];" ::"r"(addr),
-                 "f"(v.x), "f"(v.y), "r"(rbar)
-                 : "memory");
-}
-
-// The same for 16 bytes (16-byte aligned address).
+// Asynchronous store of 16 bytes into a peer CTA's shared memory (16-byte
+// aligned address); completion is counted (16 bytes of complete_tx) on the
+// peer's mbarrier `rbar`.  No fence is needed: the receiver observes the data
+// through that mbarrier.
 __device__ __forceinline__ void st_async_f4(uint32_t addr, float4 v, uint32_t rbar)
 {
     asm volatile("st.async.shared::cluster.mbarrier::complete_tx::bytes.v4.f32 [%0], {%1, %2, %3, %4}, [%5];" ::"r"(
@@ -180,13 +121,8 @@ __device__ __forceinline__ void st_async_f4(uint32_t addr, float4 v, uint32_t rb
                  : "memory");
 }
 
-// Arrive once on an mbarrier of a peer CTA (cluster shared-memory address).
-__device__ __forceinline__ void mbar_arrive_remote(uint32_t rbar)
-{
-    asm volatile("mbarrier.arrive.shared::cluster.b64 _, [%0];" ::"r"(rbar) : "memory");
-}
-
-// The same with release semantics at cluster scope: the shared-memory reads
+// Arrive once on an mbarrier of a peer CTA (cluster shared-memory address),
+// with release semantics at cluster scope: the shared-memory reads
 // this CTA made before (ordered by a CTA barrier) happen before anything a
 // peer does after observing the phase with mbar_wait_cluster_bounded.
 __device__ __forceinline__ void mbar_arrive_cluster(uint32_t rbar)

@@ -12,32 +12,22 @@
 namespace ppf {
 
 int ring_variants_c32(int N, int T, int want, KernelEntry* out);
-int cluster_variants_c32(int N, int T, int want, KernelEntry* out);
 int ring_variants_c16(int N, int T, int want, KernelEntry* out);
-int cluster_variants_c16(int N, int T, int want, KernelEntry* out);
 int ring_variants_ci8(int N, int T, int want, KernelEntry* out);
-int cluster_variants_ci8(int N, int T, int want, KernelEntry* out);
-int split_variants_c32(int N, int T, int want, KernelEntry* out);
-int twopass_variants_c32(int N, int T, int want, KernelEntry* out);
-int twopass_variants_c16(int N, int T, int want, KernelEntry* out);
-int twopass_variants_ci8(int N, int T, int want, KernelEntry* out);
 int gather_variants_c32(int N, int T, int want, KernelEntry* out);
 int gather_variants_c16(int N, int T, int want, KernelEntry* out);
 int gather_variants_ci8(int N, int T, int want, KernelEntry* out);
 int ring_variants_f16_c32(int N, int T, int want, KernelEntry* out);
-int cluster_variants_f16_c32(int N, int T, int want, KernelEntry* out);
 int gather_variants_f16_c32(int N, int T, int want, KernelEntry* out);
-static int no_variants(int, int, int, KernelEntry*) { return 0; }
 
 using VariantFn = int (*)(int, int, int, KernelEntry*);
 
 // Number of variants for (N, T, dtype); fills *out with variant `want` if it exists.
 int variants(int N, int T, int dtype, int want, KernelEntry* out)
 {
-    static const VariantFn lists[3][5] = {
-        {ring_variants_c32, cluster_variants_c32, split_variants_c32, twopass_variants_c32, gather_variants_c32},
-        {ring_variants_c16, cluster_variants_c16, no_variants, twopass_variants_c16, gather_variants_c16},
-        {ring_variants_ci8, cluster_variants_ci8, no_variants, twopass_variants_ci8, gather_variants_ci8}};
+    static const VariantFn lists[3][2] = {{ring_variants_c32, gather_variants_c32},
+                                          {ring_variants_c16, gather_variants_c16},
+                                          {ring_variants_ci8, gather_variants_ci8}};
     if (dtype < 0 || dtype > 2) return 0;
     int n = 0;
     for (VariantFn f : lists[dtype]) {
@@ -49,16 +39,31 @@ int variants(int N, int T, int dtype, int want, KernelEntry* out)
     return n;
 }
 
+// Index of the variant named `name` for (N, T, dtype), or -1.
+static int variant_by_name(int N, int T, int dtype, const char* name)
+{
+    const int n = variants(N, T, dtype, -1, nullptr);
+    for (int i = 0; i < n; ++i) {
+        KernelEntry e;
+        variants(N, T, dtype, i, &e);
+        if (e.name && std::strcmp(e.name, name) == 0) return i;
+    }
+    return -1;
+}
+
 static int tuned_variant(int N, int T, int dtype)
 {
-    // An entry applies only while its variant still has the recorded name.
+    // An entry names its tile shape; the recorded index is where the shape
+    // stood when it was timed and serves only as a first guess.  A shape that
+    // is no longer compiled falls back to variant 0.
 #define PPF_TUNED(NN, TT, DT, V, NAME)                                                      \
     if (N == NN && T == TT && dtype == DT) {                                                \
         KernelEntry e;                                                                      \
         if (V < variants(N, T, dtype, -1, nullptr) && (variants(N, T, dtype, V, &e), true) && \
             e.name && std::strcmp(e.name, NAME) == 0)                                      \
             return V;                                                                       \
-        return 0;                                                                           \
+        const int byname = variant_by_name(N, T, dtype, NAME);                              \
+        return byname >= 0 ? byname : 0;                                                    \
     }
 #if __has_include("ppf_tuned.inc")
 #include "ppf_tuned.inc"
@@ -71,7 +76,7 @@ static int tuned_variant(int N, int T, int dtype)
 // input only); an empty entry when none is compiled.
 static KernelEntry f16_twin(int N, int T, int dtype, const char* name)
 {
-    static const VariantFn lists[] = {ring_variants_f16_c32, cluster_variants_f16_c32, gather_variants_f16_c32};
+    static const VariantFn lists[] = {ring_variants_f16_c32, gather_variants_f16_c32};
     if (dtype != 0 || !name) return KernelEntry{};
     char want[112];
     std::snprintf(want, sizeof(want), "%s:f16", name);

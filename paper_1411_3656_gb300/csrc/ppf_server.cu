@@ -11,7 +11,7 @@
 //      work-list launch per specialised kernel, as in ppf_batch),
 //   3. copies each stream's new history to the front of its other buffer
 //      (one batched copy launch) and swaps the buffers.
-// The per-tick tables (copies, jobs, items, tensor maps) are written into a
+// The per-tick tables (copies, jobs, items) are written into a
 // pinned staging buffer and uploaded with one asynchronous copy; two staging
 // slots alternate so the host can build tick k+1 while tick k runs.
 #include "ppf.h"
@@ -296,7 +296,6 @@ ppf_status_t ppf_server_tick(ppf_server_t s, void* stream, int* n_done)
         ppf::PlanView view;
         ppf::KernelEntry entry;
         std::vector<ppf::PpfJob> jobs;
-        std::vector<std::vector<unsigned char>> maps;
     };
     std::map<std::string, G> groups;
     std::vector<std::string> order;
@@ -309,15 +308,13 @@ ppf_status_t ppf_server_tick(ppf_server_t s, void* stream, int* n_done)
     };
     std::vector<Single> singles;
     int processed = 0;
-    bool encode_failed = false;
     auto add_job = [&](ppf_server_s::Slot& sl, const void* in, float2* out, int64_t count) {
-        const int64_t T = sl.view.T;
         if (sl.entry.launch_work) {
             char key[160];
             std::snprintf(key, sizeof(key), "%d:%d:%d:%s", sl.view.N, sl.view.T, sl.view.dtype, sl.entry.name);
             auto it = groups.find(key);
             if (it == groups.end()) {
-                groups[key] = G{sl.view, sl.entry, {}, {}};
+                groups[key] = G{sl.view, sl.entry, {}};
                 order.push_back(key);
                 it = groups.find(key);
             }
@@ -326,11 +323,6 @@ ppf_status_t ppf_server_tick(ppf_server_t s, void* stream, int* n_done)
             j.Y = out;
             j.h = sl.view.h;
             j.S = count;
-            if (sl.entry.encode) {
-                std::vector<unsigned char> m(128, 0);
-                if (!sl.entry.encode(m.data(), in, count + T - 1)) encode_failed = true;
-                it->second.maps.push_back(std::move(m));
-            }
             it->second.jobs.push_back(j);
         } else {
             singles.push_back({sl.view, sl.entry, in, out, count});
@@ -419,12 +411,11 @@ ppf_status_t ppf_server_tick(ppf_server_t s, void* stream, int* n_done)
         sl.held = hist_len;
         sl.queue.clear();
     }
-    if (encode_failed) return PPF_ERR_INVALID_ARG;
     if (processed == 0) return PPF_OK;
 
     // 2. items for each group (about one per resident CTA or cluster)
     struct Tab {
-        size_t maps_at, jobs_at, items_at;
+        size_t jobs_at, items_at;
         std::vector<ppf::PpfItem> items;
         int grid;
     };
@@ -465,7 +456,6 @@ ppf_status_t ppf_server_tick(ppf_server_t s, void* stream, int* n_done)
             return (a.bhi - a.blo) > (b.bhi - b.blo);
         });
         tb.grid = std::min<int>(units, (int)tb.items.size()) * g.entry.cluster;
-        tb.maps_at = place(128 * g.maps.size(), 128);
         tb.jobs_at = place(sizeof(ppf::PpfJob) * g.jobs.size(), 16);
         tb.items_at = place(sizeof(ppf::PpfItem) * tb.items.size(), 16);
     }
@@ -485,10 +475,6 @@ ppf_status_t ppf_server_tick(ppf_server_t s, void* stream, int* n_done)
     for (size_t gi = 0; gi < order.size(); ++gi) {
         G& g = groups[order[gi]];
         Tab& tb = tabs[gi];
-        for (size_t m = 0; m < g.maps.size(); ++m) {
-            std::memcpy(hs + tb.maps_at + 128 * m, g.maps[m].data(), 128);
-            g.jobs[m].tmap = ds + tb.maps_at + 128 * m;
-        }
         std::memcpy(hs + tb.jobs_at, g.jobs.data(), sizeof(ppf::PpfJob) * g.jobs.size());
         std::memcpy(hs + tb.items_at, tb.items.data(), sizeof(ppf::PpfItem) * tb.items.size());
         works[gi].jobs = reinterpret_cast<const ppf::PpfJob*>(ds + tb.jobs_at);
@@ -519,8 +505,7 @@ ppf_status_t ppf_server_tick(ppf_server_t s, void* stream, int* n_done)
         e = g.entry.launch_work(g.view, works[gi], tabs[gi].grid, s->lane[w % nl]);
         ++launches;
     }
-    // jobs on kernels without a work-list form may use their plan's scratch:
-    // one lane runs them one after another
+    // jobs on the general kernel (no work-list form): one launch each, on one lane
     for (auto& sg : singles) {
         if (e != cudaSuccess) break;
         e = sg.entry.launch(sg.view, sg.in, sg.out, sg.S, s->lane[0]);
