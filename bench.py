@@ -224,6 +224,16 @@ def oracle_baseline(args, cells, x_host, budget_s):
     return value, cores, desc
 
 
+def workload_config(args, cells, samples_step, world):
+    """The `config` object of the JSON line (identical for both arms)."""
+    return {"workload": args.workload + (" (1 s of 6.5 GB/s complex64 per (N,T) cell)"
+                                         if args.workload == "realtime_sweep" else " (N=256,T=8,S=1024)"),
+            "cells": [f"{N}:{T}" for N, T in cells], "seconds_per_cell": args.seconds,
+            "input": args.dtype, "output": args.out_dtype,
+            "l2": "inputs larger than L2 (no flush needed)" if samples_step * 8 > 129e6 else "L2-resident",
+            "parallelism": f"replicas x{world}"}
+
+
 # ----------------------------------------------------------------- reference arm
 def run_reference(args):
     rank = int(os.environ.get("RANK", "0"))
@@ -237,22 +247,31 @@ def run_reference(args):
     # prefix large enough for the sampled rows of every cell
     x = make_input(args, n_max, args.dtype)
     per_step = max(0.2, args.ref_seconds / max(1, args.steps + args.warmup))
-    vals = []
+    vals, walls = [], []
     for i in range(args.warmup + args.steps):
+        t0 = time.perf_counter()
         v, cores, desc = oracle_baseline(args, cells, x, per_step)
         if i >= args.warmup:
             vals.append(v)
+            walls.append(time.perf_counter() - t0)
     value = statistics.median(vals)
     samples = sum(spectra_of(args, N, T) * N for N, T in cells)
+    world = int(os.environ.get("WORLD_SIZE", "1"))
     line = {
         "impl": "reference",
         "metric": "PPF output Msamples/s (x real time at 6.5 GB/s; HBM GB/s vs peak)",
         "value": value, "unit": "Msamples/s", "n_gpus": args.gpus, "steps": args.steps,
-        "warmup": args.warmup, "ms_per_step": samples / (value * 1e6) * 1e3,
+        "warmup": args.warmup,
+        # each step times the oracle on a bounded sample of every cell's spectra
+        # (cpu_baseline.sample): ms_per_step is that step's wall time; value is
+        # the sampled output samples per second of CPU time, and the whole
+        # workload at that rate would take workload_ms_extrapolated
+        "ms_per_step": statistics.mean(walls) * 1e3,
+        "ms_per_step_kind": "wall time of one timed step (a bounded sample of the workload)",
+        "workload_ms_extrapolated": samples / (value * 1e6) * 1e3,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
         "data": "synthetic",
-        "config": {"workload": args.workload, "cells": [f"{N}:{T}" for N, T in cells],
-                   "seconds_per_cell": args.seconds, "input": args.dtype},
+        "config": workload_config(args, cells, samples, world),
         "x_realtime": value * 1e6 / metrics.REALTIME_SAMPLES_PER_S,
         "cpu_baseline": {"value": value, "unit": "Msamples/s", "cores": cores, "kind": "oracle", "sample": desc},
         "e2e": {"value": value, "unit": "Msamples/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
@@ -479,12 +498,7 @@ def run_ours(args):
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
             "dtype": {"c32": "f32", "c16": "f16-in/f32", "ci8": "i8-in/f32"}[dtype]
             + ("/f16-out" if args.out_dtype == "f16" else ""), "data": "synthetic",
-            "config": {"workload": args.workload + (" (1 s of 6.5 GB/s complex64 per (N,T) cell)"
-                                                   if args.workload == "realtime_sweep" else " (N=256,T=8,S=1024)"),
-                       "cells": [f"{N}:{T}" for N, T in cells], "seconds_per_cell": args.seconds,
-                       "input": dtype, "output": args.out_dtype, "l2": "inputs larger than L2 (no flush needed)"
-                       if samples_step * 8 > 129e6 else "L2-resident",
-                       "parallelism": f"replicas x{world}"},
+            "config": workload_config(args, cells, samples_step, world),
             "x_realtime": data_s * args.steps / (elapsed_ms / 1e3),
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s",
                          "frac": achieved / hbm,

@@ -208,3 +208,18 @@ def rel_l2(a, b) -> float:
         return num
     return num / den
 
+
+
+def worst_spectrum_rel_l2(a, b) -> float:
+    """Largest per-spectrum relative L2 error over the rows of [S, N] arrays
+    (each row's ||a_s - b_s|| / ||b_s||; rows with ||b_s|| = 0 count their
+    absolute error).  A diagnostic beside the whole-array figure."""
+    a = np.asarray(a, dtype=np.complex128)
+    b = np.asarray(b, dtype=np.complex128)
+    if a.size == 0:
+        return 0.0
+    a = a.reshape(-1, a.shape[-1])
+    b = b.reshape(-1, b.shape[-1])
+    num = np.sqrt(np.sum(np.abs(a - b) ** 2, axis=1))
+    den = np.sqrt(np.sum(np.abs(b) ** 2, axis=1))
+    return float(np.max(np.where(den > 0, num / np.where(den > 0, den, 1.0), num)))

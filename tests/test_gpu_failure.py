@@ -35,7 +35,7 @@ def test_bounded_wait_times_out_and_reports(ppf):
     plan = ppf.Plan(N, T, h)
     Y = plan(torch.from_numpy(x).cuda(), n_spectra=S)
     torch.cuda.synchronize()
-    assert synth.rel_l2(Y.cpu().numpy(), oracle.ppf(x, h, N, T, S)) <= 1e-5
+    assert synth.rel_l2(Y.cpu().numpy(), oracle.ppf(x, h, N, T, S)) <= 1e-5, ("rel L2", "worst spectrum", synth.worst_spectrum_rel_l2(Y.cpu().numpy(), oracle.ppf(x, h, N, T, S)))
     plan.close()
 
 

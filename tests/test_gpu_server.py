@@ -2,12 +2,20 @@
 
 The defining property: a stream's spectra are the same alone and in the mix
 (bitwise: every spectrum is computed by the same kernel from the same inputs),
-and equal to ppf_execute on the stream's concatenated samples.
+and equal to ppf_execute on the stream's concatenated samples.  Each stream's
+served spectra are also compared with the FP64 oracle (relative L2 <= 1e-5,
+reduced-precision streams on their stored values with the FP16 coefficients
+the device uses): the first spectrum after admission, every spectrum whose
+window straddles a chunk boundary (history spliced onto a chunk head by the
+tick's copy segments), the last, and a seeded sample.
 """
 import numpy as np
 import pytest
 
+import oracle
 from paper_1411_3656_gb300 import synth
+
+TOL32 = 1e-5
 
 pytestmark = pytest.mark.gpu
 
@@ -35,6 +43,8 @@ class Feed:
         elif dtype == "c16":
             x = synth.to_fp16_iq(x)
         self.plan = ppf.Plan(N, T, self.h, dtype)
+        self.x_host = x
+        self.h_dev = self.h if dtype == "c32" else self.h.astype(np.float16).astype(np.float32)
         self.x = torch.from_numpy(np.ascontiguousarray(x)).cuda()
         self.N, self.T, self.dtype, self.total = N, T, dtype, total
         cuts = np.sort(g.choice(np.arange(1, total), size=chunks - 1, replace=False))
@@ -47,6 +57,24 @@ class Feed:
 
     def batch_reference(self):
         return self.plan(self.x)
+
+    def oracle_rows(self):
+        """First, last, straddling and sampled spectra of the whole stream."""
+        N, T = self.N, self.T
+        S = max(0, self.total // N - T + 1)
+        rows = {0, S - 1} | set(synth.sample_rows(S, 64).tolist())
+        for a, _ in self.bounds[1:]:  # chunk boundary at sample a
+            lo = max(0, -(-(a - T * N + 1) // N))
+            hi = min(S - 1, (a - 1) // N)
+            rows |= set(range(lo, hi + 1))
+        return np.asarray(sorted(r for r in rows if 0 <= r < S), dtype=np.int64)
+
+    def check_oracle(self, got):
+        rows = self.oracle_rows()
+        ref = oracle.ppf_rows(self.x_host, self.h_dev, self.N, self.T, rows)
+        g = got.cpu().numpy()[rows]
+        err = synth.rel_l2(g, ref)
+        assert err <= TOL32, (self.N, self.T, self.dtype, err, synth.worst_spectrum_rel_l2(g, ref))
 
 
 def _serve(ppf, feeds, schedule, max_chunk):
@@ -106,6 +134,9 @@ def test_alone_equals_mix_equals_batch(ppf):
     mixed = _serve(ppf, feeds, sched_mix, max_chunk)
     torch.cuda.synchronize()
     assert torch.equal(alone, mixed[0])
+    A.check_oracle(alone)
+    for f, got in zip(feeds, mixed):
+        f.check_oracle(got)
     for f, got in zip(feeds, mixed):
         ref = f.batch_reference()
         torch.cuda.synchronize()

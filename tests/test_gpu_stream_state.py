@@ -75,7 +75,7 @@ def test_save_restore_equals_uninterrupted(ppf, N, T, dtype):
     torch.cuda.synchronize()
     assert got.shape == batch.shape == (S, N)
     assert np.array_equal(got, batch)
-    assert synth.rel_l2(got, oracle.ppf(x, h, N, T, S)) <= (1e-5 if dtype == "c32" else 3e-3)
+    assert synth.rel_l2(got, oracle.ppf(x, h, N, T, S)) <= (1e-5 if dtype == "c32" else 3e-3), ("rel L2", "worst spectrum", synth.worst_spectrum_rel_l2(got, oracle.ppf(x, h, N, T, S)))
 
 
 def test_save_before_first_window_and_errors(ppf):
