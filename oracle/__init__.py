@@ -11,6 +11,12 @@ The arithmetic lives in ``ppf_oracle.c`` (plain C, FP64, OpenMP over spectra):
 * DFT stage, a naive O(N^2) forward DFT, unnormalised, natural bin order
   (Section 3: the DFT is a standard library FFT).
 
+A second, independent CPU path lives in ``ppf_cpu_radix2.c`` (its own
+library): the same FIR followed by an iterative radix-2 FFT.  It is pinned to
+the naive DFT (FP64 rounding, ~1e-13) and to every oracle pin, and it is the
+faster CPU baseline, standing in for the paper's CPU code with a library FFT
+(Section 3).  ``radix2()`` returns it with the same methods as the oracle.
+
 Inputs are converted exactly to FP64 from the values as stored (float32,
 float16, int8 and float32 coefficients are all exactly representable), so the
 oracle sees precisely what the GPU path sees.
@@ -27,8 +33,11 @@ import numpy as np
 _HERE = os.path.dirname(os.path.abspath(__file__))
 _SRC = os.path.join(_HERE, "ppf_oracle.c")
 _LIB = os.path.join(_HERE, "libppf_oracle.so")
+_SRC2 = os.path.join(_HERE, "ppf_cpu_radix2.c")
+_LIB2 = os.path.join(_HERE, "libppf_cpu_radix2.so")
 _lock = threading.Lock()
 _default = None
+_radix2 = None
 
 
 def _compile(src: str, out: str) -> str:
@@ -45,10 +54,12 @@ def _compile(src: str, out: str) -> str:
 
 
 def build(force: bool = False) -> str:
-    """Compile ``ppf_oracle.c`` into ``libppf_oracle.so`` (gcc -O2, no fast-math, no FMA contraction)."""
-    if not force and os.path.exists(_LIB) and os.path.getmtime(_LIB) >= os.path.getmtime(_SRC):
-        return _LIB
-    return _compile(_SRC, _LIB)
+    """Compile ``ppf_oracle.c`` into ``libppf_oracle.so`` and ``ppf_cpu_radix2.c``
+    into ``libppf_cpu_radix2.so`` (gcc -O2, no fast-math, no FMA contraction)."""
+    for src, lib in ((_SRC2, _LIB2), (_SRC, _LIB)):
+        if force or not os.path.exists(lib) or os.path.getmtime(lib) < os.path.getmtime(src):
+            _compile(src, lib)
+    return _LIB
 
 
 def to_complex128(x) -> np.ndarray:
@@ -146,12 +157,44 @@ class Oracle:
         return self.ppf(windows, h, N, T, n_spectra=rows.size, window_stride=T * N)
 
 
+class Radix2(Oracle):
+    """ctypes view of the second CPU path (FIR + iterative radix-2 FFT)."""
+
+    def __init__(self, lib_path: str):
+        lib = ctypes.CDLL(lib_path)
+        dp = ctypes.POINTER(ctypes.c_double)
+        for name in ("ppf_cpu2_fir", "ppf_cpu2_ppf"):
+            fn = getattr(lib, name)
+            fn.argtypes = [dp, ctypes.c_int64, dp, ctypes.c_int, ctypes.c_int, ctypes.c_int64, dp]
+            fn.restype = ctypes.c_int
+        lib.ppf_cpu2_fft.argtypes = [dp, ctypes.c_int, ctypes.c_int64, dp]
+        lib.ppf_cpu2_fft.restype = ctypes.c_int
+        lib.ppf_cpu2_threads.argtypes = []
+        lib.ppf_cpu2_threads.restype = ctypes.c_int
+        # the oracle's method names, bound to this library's functions
+        lib.ppf_oracle_fir = lib.ppf_cpu2_fir
+        lib.ppf_oracle_ppf = lib.ppf_cpu2_ppf
+        lib.ppf_oracle_dft = lib.ppf_cpu2_fft
+        lib.ppf_oracle_threads = lib.ppf_cpu2_threads
+        self.lib = lib
+
+
 def default() -> Oracle:
     global _default
     with _lock:
         if _default is None:
             _default = Oracle(build())
     return _default
+
+
+def radix2() -> Radix2:
+    """The second CPU path (FIR + radix-2 FFT), with the oracle's methods."""
+    global _radix2
+    with _lock:
+        if _radix2 is None:
+            build()
+            _radix2 = Radix2(_LIB2)
+    return _radix2
 
 
 def threads() -> int:
