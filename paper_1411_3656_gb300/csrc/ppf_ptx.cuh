@@ -153,4 +153,34 @@ __device__ __forceinline__ bool mbar_wait_cluster_bounded(uint64_t* bar, uint32_
     }
 }
 
+// ---------------------------------------------------------------- named barriers
+// CTA barriers over a subset of warps (barrier `id` in 1..15, `count` threads,
+// a multiple of 32).  The non-.aligned forms count every thread's arrival on
+// its own, so a warp need not be converged when it gets there.  arrive marks
+// arrival without waiting (a producer); sync waits for the barrier to
+// complete (a consumer); the memory accesses a thread made before arriving
+// are performed before the threads that complete the wait go on.
+__device__ __forceinline__ void nbar_sync(int id, int count)
+{
+    asm volatile("barrier.sync %0, %1;" ::"r"(id), "r"(count) : "memory");
+}
+__device__ __forceinline__ void nbar_arrive(int id, int count)
+{
+    asm volatile("barrier.arrive %0, %1;" ::"r"(id), "r"(count) : "memory");
+}
+// barrier.sync over `count` threads that also returns the OR of `v` over them.
+__device__ __forceinline__ bool nbar_sync_or(int id, int count, bool v)
+{
+    uint32_t r;
+    asm volatile(
+        "{\n\t.reg .pred q, o;\n\t"
+        "setp.ne.u32 q, %1, 0;\n\t"
+        "barrier.red.or.pred o, %2, %3, q;\n\t"
+        "selp.u32 %0, 1, 0, o;\n\t}"
+        : "=r"(r)
+        : "r"((uint32_t)v), "r"(id), "r"(count)
+        : "memory");
+    return r != 0;
+}
+
 }  // namespace ppf
