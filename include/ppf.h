@@ -221,9 +221,13 @@ ppf_status_t ppf_execute_noalloc(int N, int T, ppf_dtype_t dtype, const float* d
  * Batches: many independent streams (each with its own plan, so its own N, T,
  * dtype and coefficients) in as few launches as possible.  This is the
  * method's data-parallel form over streams (Section 3 processes one stream;
- * independent streams simply run side by side).  Jobs whose plans use the
- * same specialised kernel share one persistent launch over a device work list
- * of (job, spectrum band) items; jobs on the general kernel launch one by one.
+ * independent streams simply run side by side).  Every complex64 job whose
+ * (N, T) has a tile shape in the mixed-shape kernel (N >= 128 and
+ * N*T <= 16384, complex64 output, the plan's tuned default) joins ONE
+ * persistent launch over a device work list of (job, spectrum band) items of
+ * any N and T, which the CTAs take largest first as they become free.  Other
+ * jobs whose plans use the same specialised kernel share one persistent
+ * launch over their work list; jobs on the general kernel launch one by one.
  */
 typedef struct ppf_batch_s* ppf_batch_t;
 
@@ -236,6 +240,7 @@ typedef struct {
 } ppf_job_t;
 
 #define PPF_BATCH_GRAPH 1u   /* capture the launches into a CUDA graph on the first execute, replay after */
+#define PPF_BATCH_PER_KERNEL 2u  /* no mixed-shape launch: one persistent launch per specialised kernel */
 
 /*
  * ppf_batch_create -- group `jobs` by kernel, split them into spectrum bands

@@ -75,6 +75,16 @@ bool plan_info(ppf_plan_t plan, PlanView* view, KernelEntry* entry, int* bps)
     *bps = sample_bytes(plan->dtype);
     return true;
 }
+
+// A plan the mixed-shape kernel may run: complex64 in and out, its tuned
+// default kernel (no forced variant or general kernel).
+bool plan_mixable(ppf_plan_t plan)
+{
+    return plan && plan->dtype == PPF_IN_C32 &&
+           !(plan->flags & (PPF_FLAG_FIR_ONLY | PPF_FLAG_GENERIC | PPF_FLAG_OUT_F16 | 0xFF00u));
+}
+
+int plan_device(ppf_plan_t plan) { return plan ? plan->device : 0; }
 }  // namespace ppf
 
 namespace {

@@ -2,6 +2,7 @@
 // group one persistent launch over a device work list (see include/ppf.h).
 #include "ppf.h"
 #include "ppf_launch.h"
+#include "ppf_mix.h"
 
 #include <cuda_runtime.h>
 
@@ -16,6 +17,8 @@
 namespace ppf {
 // Plan internals this file needs (defined in ppf_api.cu).
 bool plan_info(ppf_plan_t plan, PlanView* view, KernelEntry* entry, int* sample_bytes);
+bool plan_mixable(ppf_plan_t plan);
+int plan_device(ppf_plan_t plan);
 }  // namespace ppf
 
 struct ppf_batch_s {
@@ -32,6 +35,11 @@ struct ppf_batch_s {
     };
     std::vector<Group> groups;
     std::vector<Single> singles;
+    // jobs of the mixed-shape kernel: one persistent launch for all of them
+    bool has_mix = false;
+    ppf::MixWork mix{};
+    int mix_grid = 0;
+    int* mix_err = nullptr;
     void* dev = nullptr;      // one allocation holding every table
     unsigned flags = 0;
     cudaStream_t cap_stream = nullptr;
@@ -52,6 +60,10 @@ bool aligned16(const void* p) { return (reinterpret_cast<uintptr_t>(p) & 15u) ==
 
 ppf_status_t enqueue(ppf_batch_s* b, cudaStream_t st)
 {
+    if (b->has_mix) {
+        cudaError_t e = ppf::mix_launch(b->mix, b->mix_grid, b->mix_err, st);
+        if (e != cudaSuccess) return from_cuda(e);
+    }
     for (auto& g : b->groups) {
         cudaError_t e = g.entry.launch_work(g.view, g.work, g.grid, st);
         if (e != cudaSuccess) return from_cuda(e);
@@ -70,7 +82,7 @@ extern "C" {
 ppf_status_t ppf_batch_create(ppf_batch_t* out, const ppf_job_t* jobs, int n_jobs, unsigned flags)
 {
     if (!out || n_jobs < 0 || (n_jobs > 0 && !jobs)) return PPF_ERR_INVALID_ARG;
-    if (flags & ~PPF_BATCH_GRAPH) return PPF_ERR_INVALID_ARG;
+    if (flags & ~(PPF_BATCH_GRAPH | PPF_BATCH_PER_KERNEL)) return PPF_ERR_INVALID_ARG;
     *out = nullptr;
     ppf_batch_s* b = new (std::nothrow) ppf_batch_s();
     if (!b) return PPF_ERR_OUT_OF_MEMORY;
@@ -84,6 +96,7 @@ ppf_status_t ppf_batch_create(ppf_batch_t* out, const ppf_job_t* jobs, int n_job
     };
     std::map<std::string, Pending> by_kernel;
     std::vector<std::string> order;
+    std::vector<int> mix_jobs;
     for (int i = 0; i < n_jobs; ++i) {
         const ppf_job_t& j = jobs[i];
         ppf::PlanView v;
@@ -101,6 +114,10 @@ ppf_status_t ppf_batch_create(ppf_batch_t* out, const ppf_job_t* jobs, int n_job
         if (!aligned16(j.d_in) || !aligned16(j.d_out)) {
             delete b;
             return PPF_ERR_MISALIGNED;
+        }
+        if (!(flags & PPF_BATCH_PER_KERNEL) && ppf::plan_mixable(j.plan) && ppf::mix_shape(v.N, v.T) >= 0) {
+            mix_jobs.push_back(i);
+            continue;
         }
         if (!e.launch_work) {
             b->singles.push_back({v, e, j});
@@ -158,6 +175,41 @@ ppf_status_t ppf_batch_create(ppf_batch_t* out, const ppf_job_t* jobs, int n_job
         bytes += sizeof(ppf::PpfJob) * L.jobs.size() + sizeof(ppf::PpfItem) * L.items.size() + 256;
     }
 
+    // 2b. the mixed-shape launch: the jobs' blocks laid end to end and cut
+    // into one segment of equal estimated work per CTA
+    std::vector<ppf::MixJob> mjobs;
+    std::vector<ppf::MixItem> mitems;
+    std::vector<int> mfirst;
+    if (!mix_jobs.empty()) {
+        cudaError_t e = ppf::mix_prepare(ppf::plan_device(jobs[mix_jobs[0]].plan), &b->mix_grid);
+        if (e != cudaSuccess) {
+            delete b;
+            return from_cuda(e);
+        }
+        std::vector<ppf::MixJobInfo> info;
+        for (int ji : mix_jobs) {
+            const ppf_job_t& j = jobs[ji];
+            ppf::PlanView v;
+            ppf::KernelEntry e2;
+            int bps = 0;
+            ppf::plan_info(j.plan, &v, &e2, &bps);
+            ppf::MixJob mj{};
+            mj.x = j.d_in;
+            mj.Y = static_cast<float2*>(j.d_out);
+            mj.h = v.h;
+            mj.tw = v.tw;
+            mj.S = j.n_spectra;
+            mj.shape = ppf::mix_shape(v.N, v.T);
+            mjobs.push_back(mj);
+            info.push_back({v.N, v.T, j.n_spectra});
+            if (!b->mix_err) b->mix_err = v.err;
+        }
+        ppf::mix_partition(info.data(), (int)info.size(), b->mix_grid, mitems, mfirst);
+        b->has_mix = !mitems.empty();
+        bytes += sizeof(ppf::MixJob) * mjobs.size() + sizeof(ppf::MixItem) * mitems.size() +
+                 sizeof(int) * mfirst.size() + 256;
+    }
+
     // 3. one device allocation for every table
     if (bytes > 0) {
         cudaError_t e = cudaMalloc(&b->dev, bytes);
@@ -191,6 +243,18 @@ ppf_status_t ppf_batch_create(ppf_batch_t* out, const ppf_job_t* jobs, int n_job
         g.grid = std::min<int>(units, g.work.n_items) * pg.entry.cluster;
         b->groups.push_back(g);
     }
+    if (b->has_mix) {
+        unsigned char* dev = static_cast<unsigned char*>(b->dev);
+        const size_t jobs_at = place(sizeof(ppf::MixJob) * mjobs.size(), 16);
+        std::memcpy(&host[jobs_at], mjobs.data(), sizeof(ppf::MixJob) * mjobs.size());
+        const size_t items_at = place(sizeof(ppf::MixItem) * mitems.size(), 16);
+        std::memcpy(&host[items_at], mitems.data(), sizeof(ppf::MixItem) * mitems.size());
+        const size_t first_at = place(sizeof(int) * mfirst.size(), 16);
+        std::memcpy(&host[first_at], mfirst.data(), sizeof(int) * mfirst.size());
+        b->mix.jobs = reinterpret_cast<const ppf::MixJob*>(dev + jobs_at);
+        b->mix.items = reinterpret_cast<const ppf::MixItem*>(dev + items_at);
+        b->mix.first = reinterpret_cast<const int*>(dev + first_at);
+    }
     if (bytes > 0) {
         cudaError_t e = cudaMemcpy(b->dev, host.data(), bytes, cudaMemcpyHostToDevice);
         if (e != cudaSuccess) {
@@ -199,7 +263,7 @@ ppf_status_t ppf_batch_create(ppf_batch_t* out, const ppf_job_t* jobs, int n_job
             return from_cuda(e);
         }
     }
-    b->launches = (int)(b->groups.size() + b->singles.size());
+    b->launches = (int)(b->groups.size() + b->singles.size()) + (b->has_mix ? 1 : 0);
     *out = b;
     return PPF_OK;
 }

@@ -48,6 +48,7 @@ class PPFJob(ctypes.Structure):
 
 
 BATCH_GRAPH = 1
+BATCH_PER_KERNEL = 2
 
 
 class PPFError(RuntimeError):
@@ -401,14 +402,14 @@ class Batch:
     tensors must stay alive (and at the same addresses) as long as the batch.
     """
 
-    def __init__(self, jobs, graph: bool = False):
+    def __init__(self, jobs, graph: bool = False, per_kernel: bool = False):
         self._keep = list(jobs)
         arr = (PPFJob * max(1, len(jobs)))()
         for i, (plan, x, y, n) in enumerate(jobs):
             arr[i] = PPFJob(plan.handle, x.data_ptr(), y.data_ptr(), int(n))
         out = ctypes.c_void_p()
-        _check(load().ppf_batch_create(ctypes.byref(out), arr, len(jobs), BATCH_GRAPH if graph else 0),
-               "ppf_batch_create")
+        flags = (BATCH_GRAPH if graph else 0) | (BATCH_PER_KERNEL if per_kernel else 0)
+        _check(load().ppf_batch_create(ctypes.byref(out), arr, len(jobs), flags), "ppf_batch_create")
         self.handle = out.value
 
     @property

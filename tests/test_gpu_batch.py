@@ -129,6 +129,7 @@ def test_batch_argument_errors(ppf):
     assert lib.ppf_batch_create(None, None, 0, 0) == 1
     assert lib.ppf_batch_create(ctypes.byref(out), None, -1, 0) == 1
     assert lib.ppf_batch_create(ctypes.byref(out), None, 0, 8) == 1
+    assert lib.ppf_batch_create(ctypes.byref(out), None, 0, 4) == 1
     assert lib.ppf_batch_create(ctypes.byref(out), None, 0, 0) == 0
     assert lib.ppf_batch_launches(out.value) == 0
     assert lib.ppf_batch_execute(out.value, None) == 0
@@ -159,3 +160,64 @@ def test_batch_mixes_fp16_and_complex64_outputs(ppf):
         ref = plan(xd, n_spectra=S)
         torch.cuda.synchronize()
         assert torch.equal(yd, ref), (plan.kernel, plan.out_f16)
+
+
+# (N, T) of every tile shape of the mixed-shape kernel (complex64, N*T <= 16K)
+MIX_SHAPES = [(128, 4), (128, 8), (128, 16), (128, 32), (256, 4), (256, 8), (256, 16), (256, 32), (512, 4),
+              (512, 8), (512, 16), (512, 32), (1024, 4), (1024, 8), (1024, 16), (2048, 4), (2048, 8), (4096, 4)]
+
+
+@pytest.mark.parametrize("graph", [False, True])
+def test_batch_mixed_shapes_one_launch(ppf, graph):
+    """Streams of every (N, T) the mixed-shape kernel takes, ragged lengths
+    (several work items per stream for the long ones), in ONE persistent
+    launch: every spectrum against the FP64 oracle and bitwise against the
+    stream's own ppf_execute (tuned default kernel)."""
+    import torch
+    g = np.random.default_rng(31)
+    specs = []
+    for N, T in MIX_SHAPES:
+        specs.append((N, T, "c32", int(g.integers(1, max(3, 24576 // N)))))
+    specs += [(256, 8, "c32", 3001), (1024, 4, "c32", 613), (4096, 4, "c32", 1), (512, 32, "c32", 0)]
+    jobs = _jobs(ppf, specs, 9500)
+    batch = ppf.Batch(jobs, graph=graph)
+    assert batch.launches == 1
+    before = ppf.ppf_launch_count()
+    batch.execute()
+    torch.cuda.synchronize()
+    if not graph:
+        assert ppf.ppf_launch_count() - before == 1
+    check_oracle(jobs)
+    for plan, xd, yd, S in jobs:
+        if S:
+            assert torch.equal(yd, plan(xd, n_spectra=S)), (plan.N, plan.T, plan.kernel)
+    # a second execution (graph replay) on new input
+    for plan, xd, yd, S in jobs:
+        xd.mul_(-0.5)
+        plan.oracle_in = (plan.oracle_in[0] * np.complex64(-0.5), plan.oracle_in[1])
+    batch.execute()
+    torch.cuda.synchronize()
+    check_oracle(jobs)
+    batch.close()
+
+
+def test_batch_per_kernel_flag(ppf):
+    """PPF_BATCH_PER_KERNEL keeps one persistent launch per specialised kernel
+    (the comparison form); results are those of the mixed launch, bitwise."""
+    import torch
+    specs = [(256, 8, "c32", 300), (1024, 8, "c32", 97), (2048, 4, "c32", 41), (512, 16, "c32", 128)]
+    jobs = _jobs(ppf, specs, 9700)
+    mixed = ppf.Batch(jobs)
+    assert mixed.launches == 1
+    mixed.execute()
+    torch.cuda.synchronize()
+    first = [yd.clone() for _, _, yd, _ in jobs]
+    per = ppf.Batch(jobs, per_kernel=True)
+    assert per.launches == len({p.kernel for p, _, _, _ in jobs})
+    per.execute()
+    torch.cuda.synchronize()
+    for (plan, xd, yd, S), y0 in zip(jobs, first):
+        assert torch.equal(yd, y0), plan.kernel
+    check_oracle(jobs)
+    mixed.close()
+    per.close()
