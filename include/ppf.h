@@ -321,6 +321,15 @@ ppf_status_t ppf_server_position(ppf_server_t s, int slot, int64_t* samples_in, 
 /* Device bytes reserved, admitted streams, launches of the last tick (any may be NULL). */
 ppf_status_t ppf_server_info(ppf_server_t s, size_t* reserved_bytes, int* streams, int* last_tick_launches);
 
+/* Ticks of the server that ran as a replay of its captured CUDA graph (the
+ * gather copy, the mixed-shape kernel, one work-list launch per other kernel
+ * group and the carry copy, all reading their tables from a fixed device
+ * area); the graph is captured on the first tick after an admit or release.
+ * A stream on the general kernel, or a tick whose tables exceed the capacity
+ * planned from the admitted streams, runs as direct launches instead.
+ * -1 for a NULL server. */
+int64_t ppf_server_graph_ticks(ppf_server_t s);
+
 /* Release every slot and the staging buffers.  Synchronises the device. */
 ppf_status_t ppf_server_destroy(ppf_server_t s);
 

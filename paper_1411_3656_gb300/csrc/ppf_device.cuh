@@ -288,7 +288,14 @@ struct PpfWork {
     const PpfJob* jobs;
     const PpfItem* items;
     int n_items;
+    // when set, the item count is read from device memory at kernel start
+    // (a launch captured in a CUDA graph replays with new tables)
+    const int* n_items_dev;
 };
+__device__ __forceinline__ int work_items(const PpfWork& wl)
+{
+    return wl.n_items_dev ? *wl.n_items_dev : wl.n_items;
+}
 
 // ------------------------------------------------------------------ FFT plan
 // Radix of pass p for a length-N row: 16 first (or N itself when N <= 16),

@@ -122,6 +122,7 @@ ppf_gather_kernel(const PpfWork wl, const float2* __restrict__ tw, int* __restri
     bool failed = false;
     // Every CTA of a cluster walks the same items, so the cluster keeps one
     // schedule of rounds and nobody waits on a CTA that has moved on.
+    const int n_items = work_items(wl);
     for (int it = cid;; it += ncl) {
         PpfJob job;
         int64_t blo, bhi;  // rounds
@@ -132,7 +133,7 @@ ppf_gather_kernel(const PpfWork wl, const float2* __restrict__ tw, int* __restri
             blo = nround * cid / ncl;
             bhi = nround * (cid + 1) / ncl;
         } else {
-            if (it >= wl.n_items) break;
+            if (it >= n_items) break;
             const PpfItem item = wl.items[it];
             job = wl.jobs[item.job];
             blo = item.blo;

@@ -235,6 +235,7 @@ ppf_ring_kernel(const PpfWork wl, const float2* __restrict__ tw, int* __restrict
     // between them.
     constexpr bool ODD = C::NBUF == 2 && fft_npass_r(N, C::R0) % 2 == 1;
     int bcount = 0;
+    const int n_items = work_items(wl);
     for (int it = blockIdx.x;; it += gridDim.x) {
         PpfJob job;
         int64_t blo, bhi;
@@ -245,7 +246,7 @@ ppf_ring_kernel(const PpfWork wl, const float2* __restrict__ tw, int* __restrict
             blo = nblk * blockIdx.x / gridDim.x;
             bhi = nblk * (blockIdx.x + 1) / gridDim.x;
         } else {
-            if (it >= wl.n_items) break;
+            if (it >= n_items) break;
             const PpfItem item = wl.items[it];
             job = wl.jobs[item.job];
             blo = item.blo;

@@ -185,7 +185,7 @@ __device__ __forceinline__ bool ws_item(const PpfWork& wl, int it, int rb, PpfJo
         bhi = nblk * (blockIdx.x + 1) / gridDim.x;
         return true;
     }
-    if (it >= wl.n_items) return false;
+    if (it >= work_items(wl)) return false;
     const PpfItem item = wl.items[it];
     job = wl.jobs[item.job];
     blo = item.blo;

@@ -37,7 +37,7 @@ EXPORTS = ("ppf_plan_create", "ppf_plan_destroy", "ppf_execute", "ppf_execute_ho
            "ppf_variant_name", "ppf_execute_noalloc", "ppf_batch_create", "ppf_batch_execute",
            "ppf_batch_launches", "ppf_batch_destroy", "ppf_server_create", "ppf_server_admit",
            "ppf_server_release", "ppf_server_submit", "ppf_server_submit_many", "ppf_server_tick", "ppf_server_position",
-           "ppf_server_info", "ppf_server_destroy", "ppf_design_coeffs", "ppf_check_timeout",
+           "ppf_server_info", "ppf_server_graph_ticks", "ppf_server_destroy", "ppf_design_coeffs", "ppf_check_timeout",
            "ppf_check_violations")
 
 
@@ -103,6 +103,7 @@ def load(path: str | None = None):
             "ppf_server_tick": ([vp, vp, ctypes.POINTER(i32)], i32),
             "ppf_server_position": ([vp, i32, ctypes.POINTER(i64), ctypes.POINTER(i64)], i32),
             "ppf_server_info": ([vp, ctypes.POINTER(ctypes.c_size_t), ctypes.POINTER(i32), ctypes.POINTER(i32)], i32),
+            "ppf_server_graph_ticks": ([vp], i64),
             "ppf_server_destroy": ([vp], i32),
             "ppf_design_coeffs": ([i32, i32, i32, ctypes.c_double, ctypes.POINTER(ctypes.c_float)], i32),
             "ppf_check_timeout": ([ctypes.c_uint, vp], i32),
@@ -503,6 +504,11 @@ class Server:
         _check(load().ppf_server_info(self.handle, ctypes.byref(r), ctypes.byref(n), ctypes.byref(l)),
                "ppf_server_info")
         return {"reserved_bytes": r.value, "streams": n.value, "last_tick_launches": l.value}
+
+    @property
+    def graph_ticks(self) -> int:
+        """Ticks that ran as a replay of the server's captured CUDA graph."""
+        return int(load().ppf_server_graph_ticks(self.handle))
 
     def close(self):
         if self.handle:

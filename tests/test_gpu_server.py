@@ -77,7 +77,7 @@ class Feed:
         assert err <= TOL32, (self.N, self.T, self.dtype, err, synth.worst_spectrum_rel_l2(g, ref))
 
 
-def _serve(ppf, feeds, schedule, max_chunk):
+def _serve(ppf, feeds, schedule, max_chunk, stats=None):
     """schedule: list of ticks, each a list of (feed index, chunk index)."""
     import torch
     srv = ppf.Server(max_streams=16, memory_budget_bytes=8 << 30)
@@ -99,6 +99,10 @@ def _serve(ppf, feeds, schedule, max_chunk):
         srv.tick()
     torch.cuda.synchronize()
     res = [torch.cat(o) if o else None for o in outs]
+    if stats is not None:
+        stats["ticks"] = sum(1 for t in schedule if t)  # a tick with nothing queued launches nothing
+        stats["graph_ticks"] = srv.graph_ticks
+        stats["launches"] = srv.info()["last_tick_launches"]
     srv.close()
     return res
 
@@ -185,3 +189,81 @@ def test_submit_errors(ppf):
     assert srv.tick() == 1
     srv.release(s)
     srv.close()
+
+
+def test_tick_is_a_graph_replay(ppf):
+    """Streams that all have a work-list kernel (every window that fits one SM
+    on the mixed-shape kernel, N*T = 64K complex64 on its cluster kernel,
+    int8 on its ring kernel): every tick replays the captured graph (gather
+    copy, mixed kernel, the other groups' work lists, carry copy) with only
+    the uploaded tables changing.  Each stream's spectra equal its own
+    ppf_execute bitwise and the FP64 oracle within 1e-5."""
+    import torch
+    rng = np.random.default_rng(8)
+    feeds = [Feed(ppf, 1024, 8, "c32", 1024 * 400 + 77, 111, 19), Feed(ppf, 256, 16, "c32", 256 * 900 + 5, 121, 15),
+             Feed(ppf, 4096, 16, "c32", 4096 * 60 + 999, 131, 9), Feed(ppf, 512, 4, "ci8", 512 * 500 + 3, 141, 13),
+             Feed(ppf, 128, 32, "c32", 128 * 2000 + 9, 151, 11), Feed(ppf, 2048, 4, "c32", 2048 * 150 + 1, 161, 7)]
+    max_chunk = max(b - a for f in feeds for a, b in f.bounds)
+    nxt = [0] * len(feeds)
+    sched = []
+    while any(nxt[f] < len(feeds[f].bounds) for f in range(len(feeds))):
+        tick = []
+        for f in range(len(feeds)):
+            for _ in range(int(rng.integers(0, 4))):
+                if nxt[f] < len(feeds[f].bounds):
+                    tick.append((f, nxt[f]))
+                    nxt[f] += 1
+        sched.append(tick)
+    stats = {}
+    got = _serve(ppf, feeds, sched, max_chunk, stats)
+    assert stats["graph_ticks"] == stats["ticks"], stats
+    # gather copy, mixed kernel, cluster kernel group, int8 ring group, carry copy
+    assert stats["launches"] == 5, stats
+    for f, y in zip(feeds, got):
+        f.check_oracle(y)
+        ref = f.batch_reference()
+        torch.cuda.synchronize()
+        assert torch.equal(y, ref), (f.N, f.T, f.dtype)
+
+
+def test_graph_recaptured_after_admit_and_release(ppf):
+    """Releasing a stream and admitting another between ticks re-captures the
+    graph; the streams that stay keep producing their exact spectra."""
+    import torch
+    A = Feed(ppf, 512, 8, "c32", 512 * 600 + 11, 171, 12)
+    B = Feed(ppf, 1024, 16, "c32", 1024 * 200 + 3, 181, 6)
+    C = Feed(ppf, 256, 4, "c32", 256 * 700 + 1, 191, 6)
+    max_chunk = max(b - a for f in (A, B, C) for a, b in f.bounds)
+    srv = ppf.Server(max_streams=4, memory_budget_bytes=8 << 30)
+    sa, sb = srv.admit(A.plan, max_chunk), srv.admit(B.plan, max_chunk)
+    outs = {0: [], 1: [], 2: []}
+    keep = []
+
+    def push(slot, f, i, key):
+        c = f.chunk(i)
+        k = srv.expected(slot, 0, c.shape[0])
+        out = torch.empty((k, f.N), dtype=torch.complex64, device="cuda")
+        assert srv.submit(slot, c, out) == 0
+        outs[key].append(out)
+        keep.append(c)
+
+    for i in range(6):
+        push(sa, A, i, 0)
+        push(sb, B, i, 1)
+        srv.tick()
+    torch.cuda.synchronize()
+    srv.release(sb)
+    sc = srv.admit(C.plan, max_chunk)
+    for i in range(6):
+        push(sa, A, 6 + i, 0)
+        push(sc, C, i, 2)
+        srv.tick()
+    torch.cuda.synchronize()
+    assert srv.graph_ticks == 12
+    srv.close()
+    for key, f in ((0, A), (1, B), (2, C)):
+        y = torch.cat(outs[key])
+        ref = f.batch_reference()
+        torch.cuda.synchronize()
+        assert torch.equal(y, ref[: y.shape[0]]), (f.N, f.T)
+        f.check_oracle(torch.cat([y, ref[y.shape[0]:]]))
