@@ -70,7 +70,9 @@ typedef enum {
 
 /* Plan flags. */
 #define PPF_FLAG_NONE 0u
-#define PPF_FLAG_FIR_ONLY 1u   /* test hook: write the FIR output y instead of Y */
+#define PPF_FLAG_FIR_ONLY 1u   /* write the FIR output y instead of Y (the first of the paper's two
+                                  passes, Section 3; a FIR-only kernel for complex64 N >= 128,
+                                  T in {4, 8, 16, 32}, else the general kernel's FIR-only form) */
 #define PPF_FLAG_GENERIC 2u    /* always use the general kernel (runtime T, any size) */
 /* Output bins as FP16 (I, Q) pairs (4 bytes per bin, rounded to nearest)
  * instead of complex64: a quarter less HBM traffic for complex64 input, 40%

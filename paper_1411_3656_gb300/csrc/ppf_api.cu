@@ -22,6 +22,7 @@ static std::atomic<int64_t> g_launches{0};
 void note_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
 
 KernelEntry select_fast_entry(int N, int T, int dtype, int variant, int out_f16);  // ppf_select.cu
+KernelEntry fir_only_entry(int N, int T, int dtype);                                // ppf_fir.cu
 
 }  // namespace ppf
 
@@ -30,9 +31,9 @@ using ppf::PlanView;
 
 struct ppf_plan_s {
     PlanView view;           // launch parameters (device pointers inside)
-    PlanView fir_view;       // FIR-only view for the generic kernel (test hook)
+    PlanView fir_view;       // FIR-only view (PPF_FLAG_FIR_ONLY)
     KernelEntry entry;       // kernel ppf_execute launches
-    KernelEntry fir_entry;   // generic kernel, used for PPF_FLAG_FIR_ONLY
+    KernelEntry fir_entry;   // FIR-only kernel (or the general kernel in FIR-only mode)
     ppf_dtype_t dtype = PPF_IN_C32;
     unsigned flags = 0;
     int device = 0;
@@ -230,7 +231,10 @@ ppf_status_t ppf_plan_create(ppf_plan_t* out, int N, int T, const float* h_host,
     p->fir_view = v;
     p->fir_view.fir_only = 1;
 
-    p->fir_entry = ppf::generic_entry(N, (int)in_dtype);
+    // FIR-only mode: the FIR-only kernel where it has a tile shape, else the
+    // general kernel's FIR-only form
+    p->fir_entry = ppf::fir_only_entry(N, T, (int)in_dtype);
+    if (!p->fir_entry.launch) p->fir_entry = ppf::generic_entry(N, (int)in_dtype);
     const int out_f16 = (flags & PPF_FLAG_OUT_F16) ? 1 : 0;
     const ppf::KernelEntry general = ppf::generic_entry(N, (int)in_dtype, out_f16);
     p->entry = (flags & PPF_FLAG_GENERIC) ? general : ppf::select_fast_entry(N, T, (int)in_dtype, variant, out_f16);

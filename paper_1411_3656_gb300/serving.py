@@ -38,11 +38,20 @@ def poisson_arrivals(n_streams: int, chunk_ms: float, duration_s: float, seed: i
     return out
 
 
-def run(n_streams: int, chunk_ms: float, shapes, dtype: str = "c32", duration_s: float = 2.0,
-        warmup_s: float = 0.3, seed: int = 1411_3656, memory_budget: int | None = None):
+# chunks are drawn from a device pool at least four times the 129 MB L2, so
+# a chunk's samples come from HBM, not from lines an earlier chunk left in L2
+L2_BYTES = 129 * 2**20
+POOL_MIN_BYTES = 4 * L2_BYTES
+
+
+def run(n_streams: int, chunk_ms: float, shapes, dtype: str = "c32", duration_s: float = 10.0,
+        warmup_s: float = 0.3, seed: int = 1411_3656, memory_budget: int | None = None,
+        pool_bytes: int = POOL_MIN_BYTES):
     """Serve ``n_streams`` real-time streams for ``duration_s`` seconds.
 
     ``shapes`` is a list of (N, T); stream i uses shapes[i % len(shapes)].
+    Chunks point at random 64-byte-aligned offsets of a device pool of at
+    least ``pool_bytes`` (default four times L2).
     Returns a dict with chunk latency percentiles, throughput, backlog and
     whether the run was sustained: every stream admitted and p99 latency
     <= chunk_ms (chunks a full stream buffer defers are retried next tick
@@ -61,8 +70,9 @@ def run(n_streams: int, chunk_ms: float, shapes, dtype: str = "c32", duration_s:
     free, total = torch.cuda.mem_get_info()
     budget = memory_budget if memory_budget is not None else int(0.6 * free)
     srv = ppf.Server(max_streams=n_streams, memory_budget_bytes=budget)
-    # device-resident sample pool (contents do not affect timing)
-    pool_samples = 4 * chunk + (1 << 20)
+    # device-resident sample pool (contents do not affect timing), larger
+    # than L2 so that chunk reads come from HBM
+    pool_samples = max(4 * chunk + (1 << 20), -(-int(pool_bytes) // bps))
     if dtype == "c32":
         pool = torch.randn(pool_samples, dtype=torch.complex64, device=dev)
     elif dtype == "c16":
@@ -165,7 +175,7 @@ def run(n_streams: int, chunk_ms: float, shapes, dtype: str = "c32", duration_s:
         "x_realtime_total": samples / duration_s / REALTIME_SAMPLES_PER_S,
         "sustained": bool(refused_admission == 0 and p99 <= chunk_ms),
         "wall_s": wall, "reserved_GB": info["reserved_bytes"] / 1e9,
-        "in_bytes_per_sample": bps,
+        "in_bytes_per_sample": bps, "pool_GB": pool_samples * bps / 1e9, "duration_s": duration_s,
         "host_ms_per_tick": 1e3 * host_tick_s / max(1, ticks),
         "gpu_ms_between_ticks_p50": float(np.percentile(gaps, 50)) if gaps else None,
         "chunks_per_tick_mean": float(np.mean(chunks_per_tick)) if chunks_per_tick else 0.0,

@@ -77,10 +77,21 @@ def test_sizes_ragged(ppf, N, T, S, generic):
     assert synth.rel_l2(Y, ref) <= TOL32, (kern, "worst spectrum", synth.worst_spectrum_rel_l2(Y, ref))
 
 
-@pytest.mark.parametrize("N,T,S", [(16, 3, 9), (256, 8, 31), (4096, 4, 3)])
+# (N, T, S): the general kernel's FIR-only form (N = 16, T = 3) and the
+# FIR-only kernel for every T it is built for, several bands per channel
+# slice and ragged last blocks
+FIR_CELLS = [(16, 3, 9), (256, 8, 31), (4096, 4, 3), (128, 4, 2203), (256, 32, 999), (512, 16, 1201),
+             (1024, 8, 611), (2048, 32, 157), (4096, 16, 97), (4096, 32, 1)]
+
+
+@pytest.mark.parametrize("N,T,S", FIR_CELLS)
 def test_fir_only_hook(ppf, N, T, S):
+    """PPF_FLAG_FIR_ONLY writes the filtered rows y (Section 2, Eq. 1) against
+    the oracle's FIR; sizes with a FIR-only tile shape use the FIR-only kernel."""
     x, h = _rand(N, T, S, 77)
     Y, kern = _run(ppf, x, h, N, T, S, flags=ppf.FLAG_FIR_ONLY)
+    if N >= 128 and T in (4, 8, 16, 32):
+        assert kern.startswith("fir:"), kern
     ref = oracle.fir(x, h, N, T, S)
     assert synth.rel_l2(Y, ref) <= TOL32, ("rel L2", "worst spectrum", synth.worst_spectrum_rel_l2(Y, ref))
 
