@@ -33,7 +33,7 @@ def cases():
         out.append((f"{N}x{T}:c32:default", N, T, "c32", "default", None))
         out.append((f"{N}x{T}:c32:generic", N, T, "c32", "generic", None))
     for dt in ("c16", "ci8"):
-        for N, T in ((1024, 8), (4096, 16), (256, 32)):
+        for N, T in ((1024, 8), (4096, 16), (256, 32), (4096, 8), (2048, 16), (1024, 32)):
             for i in range(ppf.ppf_variant_count(N, T, dt)):
                 out.append((f"{N}x{T}:{dt}:v{i}", N, T, dt, "variant", i))
     return out
