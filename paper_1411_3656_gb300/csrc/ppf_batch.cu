@@ -1,5 +1,7 @@
-// Batches of independent streams: jobs grouped by specialised kernel, each
-// group one persistent launch over a device work list (see include/ppf.h).
+// Batches of independent streams (see include/ppf.h): complex64 jobs whose
+// window fits one SM share one persistent launch of the mixed-shape kernel;
+// the other jobs are grouped by specialised kernel, each group one persistent
+// launch over a device work list.
 #include "ppf.h"
 #include "ppf_launch.h"
 #include "ppf_mix.h"
@@ -61,7 +63,9 @@ bool aligned16(const void* p) { return (reinterpret_cast<uintptr_t>(p) & 15u) ==
 ppf_status_t enqueue(ppf_batch_s* b, cudaStream_t st)
 {
     if (b->has_mix) {
-        cudaError_t e = ppf::mix_launch(b->mix, b->mix_grid, b->mix_err, st);
+        // the mixed kernel's item counter starts from zero every execution
+        cudaError_t e = cudaMemsetAsync(b->mix.next, 0, sizeof(int), st);
+        if (e == cudaSuccess) e = ppf::mix_launch(b->mix, b->mix_grid, b->mix_err, st);
         if (e != cudaSuccess) return from_cuda(e);
     }
     for (auto& g : b->groups) {
@@ -134,6 +138,14 @@ ppf_status_t ppf_batch_create(ppf_batch_t* out, const ppf_job_t* jobs, int n_job
         }
     }
 
+    if (!mix_jobs.empty()) {
+        cudaError_t e = ppf::mix_prepare(ppf::plan_device(jobs[mix_jobs[0]].plan), &b->mix_grid);
+        if (e != cudaSuccess) {
+            delete b;
+            return from_cuda(e);
+        }
+    }
+
     // 2. bands: about one item per resident CTA (or cluster) of the group
     struct Layout {
         std::vector<ppf::PpfJob> jobs;
@@ -175,17 +187,11 @@ ppf_status_t ppf_batch_create(ppf_batch_t* out, const ppf_job_t* jobs, int n_job
         bytes += sizeof(ppf::PpfJob) * L.jobs.size() + sizeof(ppf::PpfItem) * L.items.size() + 256;
     }
 
-    // 2b. the mixed-shape launch: the jobs' blocks laid end to end and cut
-    // into one segment of equal estimated work per CTA
+    // 2b. the mixed-shape launch: the jobs cut into items of about equal
+    // estimated cost, largest first
     std::vector<ppf::MixJob> mjobs;
     std::vector<ppf::MixItem> mitems;
-    std::vector<int> mfirst;
     if (!mix_jobs.empty()) {
-        cudaError_t e = ppf::mix_prepare(ppf::plan_device(jobs[mix_jobs[0]].plan), &b->mix_grid);
-        if (e != cudaSuccess) {
-            delete b;
-            return from_cuda(e);
-        }
         std::vector<ppf::MixJobInfo> info;
         for (int ji : mix_jobs) {
             const ppf_job_t& j = jobs[ji];
@@ -204,10 +210,9 @@ ppf_status_t ppf_batch_create(ppf_batch_t* out, const ppf_job_t* jobs, int n_job
             info.push_back({v.N, v.T, j.n_spectra});
             if (!b->mix_err) b->mix_err = v.err;
         }
-        ppf::mix_partition(info.data(), (int)info.size(), b->mix_grid, mitems, mfirst);
+        ppf::mix_items(info.data(), (int)info.size(), b->mix_grid, mitems);
         b->has_mix = !mitems.empty();
-        bytes += sizeof(ppf::MixJob) * mjobs.size() + sizeof(ppf::MixItem) * mitems.size() +
-                 sizeof(int) * mfirst.size() + 256;
+        bytes += sizeof(ppf::MixJob) * mjobs.size() + sizeof(ppf::MixItem) * mitems.size() + 16 + 256;
     }
 
     // 3. one device allocation for every table
@@ -249,11 +254,12 @@ ppf_status_t ppf_batch_create(ppf_batch_t* out, const ppf_job_t* jobs, int n_job
         std::memcpy(&host[jobs_at], mjobs.data(), sizeof(ppf::MixJob) * mjobs.size());
         const size_t items_at = place(sizeof(ppf::MixItem) * mitems.size(), 16);
         std::memcpy(&host[items_at], mitems.data(), sizeof(ppf::MixItem) * mitems.size());
-        const size_t first_at = place(sizeof(int) * mfirst.size(), 16);
-        std::memcpy(&host[first_at], mfirst.data(), sizeof(int) * mfirst.size());
+        const size_t next_at = place(sizeof(int), 16);
         b->mix.jobs = reinterpret_cast<const ppf::MixJob*>(dev + jobs_at);
         b->mix.items = reinterpret_cast<const ppf::MixItem*>(dev + items_at);
-        b->mix.first = reinterpret_cast<const int*>(dev + first_at);
+        b->mix.n_items = (int)mitems.size();
+        b->mix.n_items_dev = nullptr;
+        b->mix.next = reinterpret_cast<int*>(dev + next_at);
     }
     if (bytes > 0) {
         cudaError_t e = cudaMemcpy(b->dev, host.data(), bytes, cudaMemcpyHostToDevice);

@@ -3,6 +3,8 @@
 #include "ppf_mix.cuh"
 #include "ppf_mix.h"
 
+#include <algorithm>
+
 namespace ppf {
 
 namespace {
@@ -27,11 +29,23 @@ int shape_rb(int s)
         return 0;
     }
 }
+template <int I = 0>
+int shape_cost(int s)
+{
+    if constexpr (I < kMixShapes) {
+        using Sh = typename std::tuple_element<I, MixShapeList>::type;
+        return s == I ? Sh::COST : shape_cost<I + 1>(s);
+    } else {
+        return 0;
+    }
+}
 }  // namespace
 
 int mix_shape(int N, int T) { return shape_index(N, T); }
 
 int mix_rows_per_block(int shape) { return shape_rb(shape); }
+
+double mix_cost_ms(int shape) { return shape_cost(shape) * 1e-3; }
 
 cudaError_t mix_prepare(int device, int* grid)
 {
@@ -53,10 +67,9 @@ cudaError_t mix_launch(const MixWork& w, int grid, int* err, cudaStream_t st)
     return cudaGetLastError();
 }
 
-void mix_partition(const MixJobInfo* jobs, int n_jobs, int grid, std::vector<MixItem>& items, std::vector<int>& first)
+void mix_items(const MixJobInfo* jobs, int n_jobs, int grid, std::vector<MixItem>& items)
 {
     items.clear();
-    first.assign((size_t)grid + 1, 0);
     std::vector<double> per_block((size_t)n_jobs, 0.0);
     std::vector<int64_t> nblk((size_t)n_jobs, 0);
     double total = 0;
@@ -65,32 +78,36 @@ void mix_partition(const MixJobInfo* jobs, int n_jobs, int grid, std::vector<Mix
         if (shape < 0 || jobs[k].S <= 0) continue;
         const int RB = mix_rows_per_block(shape);
         nblk[k] = (jobs[k].S + RB - 1) / RB;
-        per_block[k] = (double)RB * jobs[k].N * (16.0 + 0.5 * jobs[k].T);
+        per_block[k] = (double)RB * jobs[k].N * mix_cost_ms(shape);
         total += per_block[k] * (double)nblk[k];
     }
-    // walk the blocks of all jobs in order; CTA c takes the blocks whose
-    // cumulative work lies in [c, c+1) * total / grid
-    int c = 0;
-    double done = 0;  // work before the current block
+    const double target = total / ((double)grid * kMixItemsPerCta);
+    std::vector<double> cost;
     for (int k = 0; k < n_jobs; ++k) {
-        int64_t b = 0;
-        while (b < nblk[k]) {
-            while (c < grid - 1 && done >= total * (c + 1) / grid) first[(size_t)++c] = (int)items.size();
-            // blocks of job k that still fit CTA c's share (at least one)
-            const double room = c == grid - 1 ? 1e300 : total * (c + 1) / grid - done;
-            int64_t take = (int64_t)(room / per_block[k] + 0.5);
-            if (take < 1) take = 1;
-            if (take > nblk[k] - b) take = nblk[k] - b;
+        if (nblk[k] == 0) continue;
+        const int RB = mix_rows_per_block(mix_shape(jobs[k].N, jobs[k].T));
+        // at least 4T spectra per item: the T-1 halo rows and the ring's
+        // fill stay small against the item's work
+        const int64_t min_len = std::max<int64_t>(2, (4 * (int64_t)jobs[k].T + RB - 1) / RB);
+        int64_t len = std::max<int64_t>(min_len, (int64_t)(target / per_block[k] + 0.5));
+        const int64_t pieces = std::max<int64_t>(1, (nblk[k] + len / 2) / len);
+        for (int64_t q = 0; q < pieces; ++q) {
             MixItem it{};
             it.job = k;
-            it.blo = b;
-            it.bhi = b + take;
-            items.push_back(it);
-            b += take;
-            done += per_block[k] * (double)take;
+            it.blo = nblk[k] * q / pieces;
+            it.bhi = nblk[k] * (q + 1) / pieces;
+            if (it.bhi > it.blo) {
+                items.push_back(it);
+                cost.push_back(per_block[k] * (double)(it.bhi - it.blo));
+            }
         }
     }
-    while (c < grid) first[(size_t)++c] = (int)items.size();
+    std::vector<size_t> order(items.size());
+    for (size_t i = 0; i < order.size(); ++i) order[i] = i;
+    std::stable_sort(order.begin(), order.end(), [&](size_t a, size_t b) { return cost[a] > cost[b]; });
+    std::vector<MixItem> sorted(items.size());
+    for (size_t i = 0; i < order.size(); ++i) sorted[i] = items[order[i]];
+    items.swap(sorted);
 }
 
 }  // namespace ppf

@@ -10,10 +10,13 @@
 // output rows, twiddle table).  The FFT warps only follow the records:
 // they switch to the record's shape (its pass twiddles stay in registers
 // while consecutive blocks keep that shape), transform the rows and store the
-// spectra.  A record with shape -1 ends the launch.  Shared memory is sized
-// for the largest shape: the ring of the largest shape and two FFT buffers at
-// fixed offsets, so buffers of consecutive blocks of different shapes never
-// overlap.
+// spectra.  A record with shape -1 ends the launch.  Shared memory holds the
+// ring at the bottom and two FFT buffer slots, each as large as the largest
+// shape's buffer, at the top; a shape's buffer lies at the end of its slot.
+// Rings up to the slots' start never touch a buffer, so items of different
+// shapes follow each other with no wait; the few rings that reach into slot 0
+// (never into the shape's own buffer there) first wait until the FFT warps
+// have finished every earlier block.
 #pragma once
 
 #include <tuple>
@@ -26,32 +29,38 @@
 
 namespace ppf {
 
-template <int N_, int T_, int RB_, int NCH_, int CPT_, int PD_ = 2>
+// COST: the shape's time in this kernel for one second of 6.5 GB/s input
+// (8.125e8 output samples), in microseconds, measured on a GB300 with one job
+// per launch; the host cuts the work into equal-cost segments with it.
+template <int N_, int T_, int RB_, int NCH_, int CPT_, int COST_, int PD_ = 1>
 struct MixShape {
-    static constexpr int N = N_, T = T_, RB = RB_, NCH = NCH_, CPT = CPT_, PD = PD_;
+    static constexpr int N = N_, T = T_, RB = RB_, NCH = NCH_, CPT = CPT_, PD = PD_, COST = COST_;
 };
 
-// The tile shapes of the mixed kernel: every complex64 (N, T) whose T-row
-// window fits one SM (N*T <= 16K), N >= 128.
+// The tile shapes of the mixed kernel: every complex64 (N, T) with
+// 128 <= N <= 2048 whose T-row window fits one SM (N*T <= 16K).
 using MixShapeList = std::tuple<
-    MixShape<128, 4, 16, 4, 2, 1>, MixShape<128, 8, 16, 4, 2, 1>, MixShape<128, 16, 16, 4, 2, 1>,
-    MixShape<128, 32, 16, 4, 2, 1>,
-    MixShape<256, 4, 8, 4, 2, 1>, MixShape<256, 8, 8, 4, 2, 1>, MixShape<256, 16, 8, 4, 2, 1>,
-    MixShape<256, 32, 8, 6, 1, 1>,
-    MixShape<512, 4, 8, 4, 2>, MixShape<512, 8, 8, 4, 2>, MixShape<512, 16, 8, 4, 2>, MixShape<512, 32, 4, 10, 2>,
-    MixShape<1024, 4, 4, 4, 2>, MixShape<1024, 8, 4, 4, 2>, MixShape<1024, 16, 2, 10, 2>,
-    MixShape<2048, 4, 2, 4, 2>, MixShape<2048, 8, 1, 9, 2>, MixShape<4096, 4, 1, 5, 2>>;
+    MixShape<128, 4, 32, 4, 2, 1990>, MixShape<128, 8, 32, 4, 2, 2010>, MixShape<128, 16, 32, 4, 2, 2320>,
+    MixShape<128, 32, 32, 4, 2, 3180>,
+    MixShape<256, 4, 16, 4, 2, 2000>, MixShape<256, 8, 16, 4, 2, 2000>, MixShape<256, 16, 16, 4, 2, 2130>,
+    MixShape<256, 32, 16, 4, 1, 2910>,
+    MixShape<512, 4, 8, 4, 2, 2156>, MixShape<512, 8, 8, 4, 2, 2185>, MixShape<512, 16, 8, 4, 2, 2451>,
+    MixShape<512, 32, 4, 10, 2, 3694>,
+    MixShape<1024, 4, 4, 4, 2, 2265>, MixShape<1024, 8, 4, 4, 2, 2335>, MixShape<1024, 16, 2, 10, 2, 3628>,
+    MixShape<2048, 4, 2, 4, 2, 2353>, MixShape<2048, 8, 1, 9, 2, 3520>>;
 constexpr int kMixShapes = (int)std::tuple_size<MixShapeList>::value;
 
-// Launch geometry shared by every shape.
+// Launch geometry shared by every shape: [ring | slot 0 | slot 1 | records |
+// mbarriers].
 struct MixGeom {
     static constexpr int NF = 256, NX = 128, NT = NF + NX;
     static constexpr int NCHMAX = 10;
-    static constexpr int BUF_BYTES = 33792;   // the largest RB * RS * 8 (RB * N = 4096, RS = N + N/32)
-    static constexpr int RING_BYTES = 163840; // the largest ring (NCH * RB * N * 8)
-    static constexpr int REC_OFF = RING_BYTES + 2 * BUF_BYTES;
-    static constexpr int SMEM = REC_OFF + 2 * 32 + NCHMAX * 8 + 16;
-    static_assert(SMEM <= 232448, "shared memory per CTA");
+    static constexpr int BUF_BYTES = 34816;   // the largest RB * RS * 8 (RB * N = 4096, RS = N + N/16)
+    static constexpr int TAIL = 2 * 32 + NCHMAX * 8 + 16;
+    static constexpr int SMEM = 232448;
+    static constexpr int SLOT0 = SMEM - TAIL - 2 * BUF_BYTES;  // = the largest ring that needs no wait
+    static constexpr int REC_OFF = SLOT0 + 2 * BUF_BYTES;
+    static_assert(SLOT0 % 16 == 0 && REC_OFF % 16 == 0, "16-byte aligned regions");
 };
 
 // A shape's configuration inside the mixed kernel (the ws layout with the
@@ -59,10 +68,26 @@ struct MixGeom {
 template <class Sh>
 struct MixCfg : WsCfg<Sh::N, Sh::T, InC32, MixGeom::NF, MixGeom::NX, Sh::RB, Sh::NCH, Sh::CPT, float2, Sh::PD> {
     using Base = WsCfg<Sh::N, Sh::T, InC32, MixGeom::NF, MixGeom::NX, Sh::RB, Sh::NCH, Sh::CPT, float2, Sh::PD>;
-    static_assert(Base::RING_BYTES <= MixGeom::RING_BYTES, "ring larger than the mixed kernel's");
+    // a ring beyond slot 0's start drains the FFT warps first
+    static constexpr bool DRAIN = Base::RING_BYTES > MixGeom::SLOT0;
     static_assert(Base::BUF_SLOTS * 8 <= MixGeom::BUF_BYTES, "FFT buffer larger than the mixed kernel's");
+    static_assert(Base::RING_BYTES <= MixGeom::SLOT0 + MixGeom::BUF_BYTES - Base::BUF_SLOTS * 8,
+                  "ring overlaps the shape's own buffer in slot 0");
     static_assert(Sh::NCH <= MixGeom::NCHMAX, "more ring chunks than mbarriers");
 };
+
+// Start of a shape's FFT buffer j (RB * RS float2 at the end of slot j).
+__device__ __forceinline__ float2* mix_buf(unsigned char* smem, int j, int slots)
+{
+    return reinterpret_cast<float2*>(smem + MixGeom::SLOT0 + (j + 1) * MixGeom::BUF_BYTES - slots * 8);
+}
+
+// The FIR warps wait (EMPTY named barriers, in block order) until the FFT
+// warps have finished with every block before `upto`.
+__device__ __forceinline__ void mix_consume_empty(int& emptied, int upto)
+{
+    for (; emptied < upto; ++emptied) nbar_sync(kBarEmpty0 + (emptied & 1), MixGeom::NT);
+}
 
 // What the FFT warps need for one block (written by FIR thread 0 next to
 // the buffer, read after the FULL barrier).
@@ -199,9 +224,8 @@ struct MixFft {
     static constexpr int RS = PD == 1 ? fft_row_stride(N) : N + (N / 32 > 2 ? N / 32 : 2);
     static_assert(RB * RS * 8 <= MixGeom::BUF_BYTES, "FFT buffer larger than the mixed kernel's");
 };
-using MixFftList = std::tuple<MixFft<128, 16, 1>, MixFft<256, 8, 1>, MixFft<512, 8, 2>, MixFft<512, 4, 2>,
-                              MixFft<1024, 4, 2>, MixFft<1024, 2, 2>, MixFft<2048, 2, 2>, MixFft<2048, 1, 2>,
-                              MixFft<4096, 1, 2>>;
+using MixFftList = std::tuple<MixFft<128, 32, 1>, MixFft<256, 16, 1>, MixFft<512, 8, 1>, MixFft<512, 4, 1>,
+                              MixFft<1024, 4, 1>, MixFft<1024, 2, 1>, MixFft<2048, 2, 1>, MixFft<2048, 1, 1>>;
 constexpr int kMixFfts = (int)std::tuple_size<MixFftList>::value;
 
 template <int I = 0>
@@ -221,8 +245,8 @@ __host__ __device__ constexpr int mix_fft_index(int N, int RB)
 // phase parity.
 template <class C>
 __device__ __forceinline__ void mix_fir_item(const MixJob& job, int64_t blo, int64_t bhi, int shape,
-                                             unsigned char* ring, float2* X, MixRec* rec, uint64_t* bars,
-                                             uint32_t& ph, int& gb, bool& failed)
+                                             unsigned char* ring, MixRec* rec, uint64_t* bars, uint32_t& ph,
+                                             int& gb, int& emptied, bool& failed)
 {
     constexpr int N = C::N, T = C::T, NF = C::NF, RB = C::RB, NCH = C::NCH;
     constexpr int G = C::G, RBT = C::RBT, BPS = C::BPS, RING_ROWS = C::RING_ROWS, RS = C::RS;
@@ -240,6 +264,8 @@ __device__ __forceinline__ void mix_fir_item(const MixJob& job, int64_t blo, int
     const int64_t s_hi = S < bhi * RB ? S : bhi * RB;
     const int64_t in_end = s_hi + T - 1;
     const int nchunks = (int)((in_end - s_lo + RB - 1) / RB);
+    // this ring reaches into slot 0: every earlier block leaves the buffers first
+    if constexpr (C::DRAIN) mix_consume_empty(emptied, gb);
 
     int issued = 0;
     auto issue = [&](int k) {
@@ -293,8 +319,9 @@ __device__ __forceinline__ void mix_fir_item(const MixJob& job, int64_t blo, int
             ph ^= 1u << slot;
         }
         const int j = gb & 1;
-        if (gb >= 2) nbar_sync(kBarEmpty0 + j, C::NT);
-        float2* const fb = X + j * (MixGeom::BUF_BYTES / 8);
+        // the FFT warps have finished the block before last (buffer j)
+        mix_consume_empty(emptied, gb - 1);
+        float2* const fb = mix_buf(ring, j, C::BUF_SLOTS);
         constexpr int NW = (RBT + T - 2) / RB + 1;
         uint32_t cbase_off[C::RG == 1 ? NW : 1];
         if constexpr (C::RG == 1) {
@@ -407,36 +434,47 @@ __device__ __forceinline__ void mix_fir_item(const MixJob& job, int64_t blo, int
 
 template <int I = 0>
 __device__ __forceinline__ void mix_fir_dispatch(int shape, const MixJob& job, int64_t blo, int64_t bhi,
-                                                 unsigned char* ring, float2* X, MixRec* rec, uint64_t* bars,
-                                                 uint32_t& ph, int& gb, bool& failed)
+                                                 unsigned char* ring, MixRec* rec, uint64_t* bars, uint32_t& ph,
+                                                 int& gb, int& emptied, bool& failed)
 {
     if constexpr (I < kMixShapes) {
         if (shape == I) {
             using Sh = typename std::tuple_element<I, MixShapeList>::type;
-            mix_fir_item<MixCfg<Sh>>(job, blo, bhi, I, ring, X, rec, bars, ph, gb, failed);
+            mix_fir_item<MixCfg<Sh>>(job, blo, bhi, I, ring, rec, bars, ph, gb, emptied, failed);
         } else {
-            mix_fir_dispatch<I + 1>(shape, job, blo, bhi, ring, X, rec, bars, ph, gb, failed);
+            mix_fir_dispatch<I + 1>(shape, job, blo, bhi, ring, rec, bars, ph, gb, emptied, failed);
         }
     }
 }
 
-__device__ __forceinline__ void mix_fir_role(const MixWork& w, unsigned char* ring, float2* X, MixRec* rec,
-                                             uint64_t* bars, int* __restrict__ err)
+__device__ __forceinline__ void mix_fir_role(const MixWork& w, unsigned char* ring, MixRec* rec, uint64_t* bars,
+                                             int* __restrict__ err)
 {
     const int tid = threadIdx.x;
     uint32_t ph = 0;
-    int gb = 0;
+    int gb = 0;       // blocks handed to the FFT warps
+    int emptied = 0;  // blocks the FFT warps are known to have finished
     bool failed = false;
-    const int it_end = w.first[blockIdx.x + 1];
-    for (int it = w.first[blockIdx.x]; it < it_end; ++it) {
+    const int n_items = w.n_items_dev ? *w.n_items_dev : w.n_items;
+    int* next_item = reinterpret_cast<int*>(reinterpret_cast<unsigned char*>(bars) + MixGeom::NCHMAX * 8);
+    int par = 0;
+    for (int it = blockIdx.x; it < n_items;) {
+        // the CTA's next item, asked for now so the answer is there when this one ends
+        int pref = 0;
+        if (tid == 0) pref = (int)gridDim.x + atomicAdd(w.next, 1);
         const MixItem item = w.items[it];
         const MixJob job = w.jobs[item.job];
-        if (item.blo >= item.bhi || job.shape < 0 || job.shape >= kMixShapes) continue;
-        mix_fir_dispatch(job.shape, job, item.blo, item.bhi, ring, X, rec, bars, ph, gb, failed);
+        if (item.blo < item.bhi && job.shape >= 0 && job.shape < kMixShapes)
+            mix_fir_dispatch(job.shape, job, item.blo, item.bhi, ring, rec, bars, ph, gb, emptied, failed);
+        if (tid == 0) next_item[par] = pref;
+        nbar_sync(kBarFir, MixGeom::NF);
+        it = next_item[par];
+        par ^= 1;
     }
-    // the end record, then the EMPTY arrival of the last block
+    // the end record (in the slot of block gb), then the EMPTY arrivals of
+    // the blocks still outstanding
     const int j = gb & 1;
-    if (gb >= 2) nbar_sync(kBarEmpty0 + j, MixGeom::NT);
+    mix_consume_empty(emptied, gb - 1);
     if (tid == 0) {
         MixRec r{};
         r.shape = -1;
@@ -444,7 +482,7 @@ __device__ __forceinline__ void mix_fir_role(const MixWork& w, unsigned char* ri
         rec[j] = r;
     }
     nbar_arrive(kBarFull0 + j, MixGeom::NT);
-    if (gb >= 1) nbar_sync(kBarEmpty0 + ((gb - 1) & 1), MixGeom::NT);
+    mix_consume_empty(emptied, gb);
     if (failed && tid == 0) atomicExch(err, 1);
 }
 
@@ -453,7 +491,7 @@ __device__ __forceinline__ void mix_fir_role(const MixWork& w, unsigned char* ri
 // path (or the end record) arrives, returned in r with gb its block; the
 // pass twiddles stay in registers meanwhile.
 template <int I>
-__device__ __forceinline__ void mix_fft_run(float2* X, const MixRec* rec, MixRec& r, int& gb)
+__device__ __forceinline__ void mix_fft_run(unsigned char* smem, const MixRec* rec, MixRec& r, int& gb)
 {
     using F = typename std::tuple_element<I, MixFftList>::type;
     constexpr int N = F::N, NX = MixGeom::NX;
@@ -467,7 +505,7 @@ __device__ __forceinline__ void mix_fft_run(float2* X, const MixRec* rec, MixRec
             twr.load(tw, lt);
         }
         const int j = gb & 1;
-        mix_fft_rows<N, F::RB, NX, F::RS, F::PD>(X + j * (MixGeom::BUF_BYTES / 8), twr, tw, r.Y, r.rows, r.rb, lt,
+        mix_fft_rows<N, F::RB, NX, F::RS, F::PD>(mix_buf(smem, j, F::RB * F::RS), twr, tw, r.Y, r.rows, r.rb, lt,
                                                  kBarEmpty0 + j);
         ++gb;
         const int jn = gb & 1;
@@ -477,27 +515,26 @@ __device__ __forceinline__ void mix_fft_run(float2* X, const MixRec* rec, MixRec
 }
 
 template <int I = 0>
-__device__ __forceinline__ void mix_fft_dispatch(float2* X, const MixRec* rec, MixRec& r, int& gb)
+__device__ __forceinline__ void mix_fft_dispatch(unsigned char* smem, const MixRec* rec, MixRec& r, int& gb)
 {
     if constexpr (I < kMixFfts) {
-        if (r.ni == I) mix_fft_run<I>(X, rec, r, gb);
-        else mix_fft_dispatch<I + 1>(X, rec, r, gb);
+        if (r.ni == I) mix_fft_run<I>(smem, rec, r, gb);
+        else mix_fft_dispatch<I + 1>(smem, rec, r, gb);
     }
 }
 
-__device__ __forceinline__ void mix_fft_role(float2* X, const MixRec* rec)
+__device__ __forceinline__ void mix_fft_role(unsigned char* smem, const MixRec* rec)
 {
     int gb = 0;
     nbar_sync(kBarFull0, MixGeom::NT);
     MixRec r = rec[0];
-    while (r.shape >= 0 && r.ni >= 0 && r.ni < kMixFfts) mix_fft_dispatch(X, rec, r, gb);
+    while (r.shape >= 0 && r.ni >= 0 && r.ni < kMixFfts) mix_fft_dispatch(smem, rec, r, gb);
 }
 
 __global__ void __launch_bounds__(MixGeom::NT, 1) ppf_mix_kernel(const MixWork w, int* __restrict__ err)
 {
     extern __shared__ __align__(128) unsigned char smem[];
     unsigned char* ring = smem;
-    float2* X = reinterpret_cast<float2*>(smem + MixGeom::RING_BYTES);
     MixRec* rec = reinterpret_cast<MixRec*>(smem + MixGeom::REC_OFF);
     uint64_t* bars = reinterpret_cast<uint64_t*>(smem + MixGeom::REC_OFF + 2 * sizeof(MixRec));
     if (threadIdx.x == 0) {
@@ -505,8 +542,8 @@ __global__ void __launch_bounds__(MixGeom::NT, 1) ppf_mix_kernel(const MixWork w
         fence_mbar_init();
     }
     __syncthreads();
-    if (threadIdx.x < MixGeom::NF) mix_fir_role(w, ring, X, rec, bars, err);
-    else mix_fft_role(X, rec);
+    if (threadIdx.x < MixGeom::NF) mix_fir_role(w, ring, rec, bars, err);
+    else mix_fft_role(smem, rec);
 }
 
 }  // namespace ppf

@@ -29,13 +29,16 @@ struct MixItem {
     int64_t blo;
     int64_t bhi;
 };
-// CTA c processes items[first[c] .. first[c+1]) in order: the host cuts the
-// jobs' blocks, laid end to end, into one segment of equal estimated work per
-// CTA (a segment may span several jobs: one item per job piece).
+// The work of one launch.  CTA c takes item c first; every later item goes to
+// the CTA that asks for it next (an atomic counter), so CTAs that finish
+// early take more items.  Items are sorted by estimated cost, largest first.
 struct MixWork {
     const MixJob* jobs;
     const MixItem* items;
-    const int* first;  // [grid + 1]
+    int n_items;             // used when n_items_dev is null
+    int pad;
+    const int* n_items_dev;  // item count read on the device (graph replays)
+    int* next;               // items handed out beyond the first gridDim.x: zero before each launch
 };
 
 // Index of (N, T) in the kernel's shape list (complex64 input and output),
@@ -43,19 +46,23 @@ struct MixWork {
 int mix_shape(int N, int T);
 // Spectra per block of a shape.
 int mix_rows_per_block(int shape);
+// Measured time of a shape in the mixed kernel for one second of 6.5 GB/s
+// input (ms): the relative cost of its samples.
+double mix_cost_ms(int shape);
 // Kernel attributes; *grid = resident CTAs on `device` (one per SM).
 cudaError_t mix_prepare(int device, int* grid);
 // Launch `grid` CTAs over the work list.
 cudaError_t mix_launch(const MixWork& w, int grid, int* err, cudaStream_t st);
 
-// Host: split `jobs` into items, one contiguous segment of about equal
-// estimated work (output samples weighted by 16 + T/2) per CTA of `grid`;
-// items and first (grid + 1 entries) are filled.
+// Host: cut `jobs` into items of about equal estimated cost (output samples
+// weighted by the shape's measured cost), about kMixItemsPerCta per CTA of
+// `grid` and never shorter than the window's halo calls for, sorted largest
+// first.
 struct MixJobInfo {
     int N, T;
     int64_t S;
 };
-void mix_partition(const MixJobInfo* jobs, int n_jobs, int grid, std::vector<MixItem>& items,
-                   std::vector<int>& first);
+constexpr int kMixItemsPerCta = 12;
+void mix_items(const MixJobInfo* jobs, int n_jobs, int grid, std::vector<MixItem>& items);
 
 }  // namespace ppf

@@ -129,7 +129,7 @@ struct ppf_server_s {
     // the tick as a CUDA graph: fixed device tables (capacities from the
     // admitted streams), re-captured when a stream is admitted or released
     struct Layout {
-        size_t counts_at = 0, gather_at = 0, carry_at = 0, mjobs_at = 0, mitems_at = 0, mfirst_at = 0, bytes = 0;
+        size_t counts_at = 0, gather_at = 0, carry_at = 0, mjobs_at = 0, mitems_at = 0, mnext_at = 0, bytes = 0;
         int cap_gather = 0, cap_carry = 0, cap_mjobs = 0, cap_mitems = 0;
         bool has_mix = false;
         int mix_grid = 0;
@@ -230,7 +230,7 @@ bool build_layout(ppf_server_s* s)
             L.cap_gjobs[it->second] += 8;
         }
     }
-    L.cap_mitems = L.cap_mjobs + L.mix_grid + 1;
+    L.cap_mitems = L.cap_mjobs + (ppf::kMixItemsPerCta + 4) * L.mix_grid;
     for (size_t g = 0; g < L.keys.size(); ++g) {
         const int units = L.ggrid[g] / L.gentry[g].cluster;
         L.cap_gitems.push_back(L.cap_gjobs[g] + 4 * units + 8);
@@ -242,12 +242,12 @@ bool build_layout(ppf_server_s* s)
         off += n;
         return at;
     };
-    L.counts_at = place(sizeof(int) * (2 + L.keys.size()));
+    L.counts_at = place(sizeof(int) * (3 + L.keys.size()));
     L.gather_at = place(sizeof(CopySeg) * L.cap_gather);
     L.carry_at = place(sizeof(CopySeg) * L.cap_carry);
     L.mjobs_at = place(sizeof(ppf::MixJob) * L.cap_mjobs);
     L.mitems_at = place(sizeof(ppf::MixItem) * L.cap_mitems);
-    L.mfirst_at = place(sizeof(int) * (L.mix_grid + 1));
+    L.mnext_at = place(sizeof(int) * 4);
     for (size_t g = 0; g < L.keys.size(); ++g) {
         L.gjobs_at.push_back(place(sizeof(ppf::PpfJob) * L.cap_gjobs[g]));
         L.gitems_at.push_back(place(sizeof(ppf::PpfItem) * L.cap_gitems[g]));
@@ -280,7 +280,8 @@ cudaError_t enqueue_graph_tick(ppf_server_s* s, cudaStream_t st, int* launches)
         ppf::MixWork mw{};
         mw.jobs = reinterpret_cast<const ppf::MixJob*>(d + L.mjobs_at);
         mw.items = reinterpret_cast<const ppf::MixItem*>(d + L.mitems_at);
-        mw.first = reinterpret_cast<const int*>(d + L.mfirst_at);
+        mw.n_items_dev = counts + 2 + (int)L.keys.size();
+        mw.next = reinterpret_cast<int*>(d + L.mnext_at);
         e = ppf::mix_launch(mw, L.mix_grid, L.mix_err, s->lane[w++ % nl]);
         ++n;
     }
@@ -642,8 +643,7 @@ ppf_status_t ppf_server_tick(ppf_server_t s, void* stream, int* n_done)
     // 2. item lists: the mixed kernel's per-CTA segments; per kernel group,
     //    pieces of about a quarter of a unit's share, largest first
     std::vector<ppf::MixItem> mitems;
-    std::vector<int> mfirst((size_t)s->mix_grid + 1, 0);
-    if (!mjobs.empty()) ppf::mix_partition(minfo.data(), (int)minfo.size(), s->mix_grid, mitems, mfirst);
+    if (!mjobs.empty()) ppf::mix_items(minfo.data(), (int)minfo.size(), s->mix_grid, mitems);
     auto group_items = [&](const G& g, std::vector<ppf::PpfItem>& items) {
         const int RB = g.entry.rows_per_block;
         const int units = std::max(1, g.view.grid_cap / g.entry.cluster);
@@ -700,10 +700,12 @@ ppf_status_t ppf_server_tick(ppf_server_t s, void* stream, int* n_done)
             if (e != cudaSuccess) return from_cuda(e);
             unsigned char* h = s->tab_host[k];
             unsigned char* d = s->tab_dev;
-            std::vector<int> counts(2 + L.keys.size());
+            std::vector<int> counts(3 + L.keys.size());
             counts[0] = (int)gather.size();
             counts[1] = (int)carry.size();
             for (size_t g = 0; g < L.keys.size(); ++g) counts[2 + g] = (int)gitems[g].size();
+            counts[2 + L.keys.size()] = (int)mitems.size();
+            const int zero4[4] = {0, 0, 0, 0};
             auto stage = [&](size_t at, const void* src, size_t n) {
                 if (n == 0 || e != cudaSuccess) return;
                 std::memcpy(h + at, src, n);
@@ -715,7 +717,7 @@ ppf_status_t ppf_server_tick(ppf_server_t s, void* stream, int* n_done)
             if (L.has_mix) {
                 stage(L.mjobs_at, mjobs.data(), sizeof(ppf::MixJob) * mjobs.size());
                 stage(L.mitems_at, mitems.data(), sizeof(ppf::MixItem) * mitems.size());
-                stage(L.mfirst_at, mfirst.data(), sizeof(int) * mfirst.size());
+                stage(L.mnext_at, zero4, sizeof(zero4));  // the item counter starts from zero
             }
             for (size_t g = 0; g < L.keys.size(); ++g) {
                 if (!gsrc[g]) continue;
@@ -752,7 +754,7 @@ ppf_status_t ppf_server_tick(ppf_server_t s, void* stream, int* n_done)
     const size_t carry_at = place(sizeof(CopySeg) * carry.size(), 16);
     const size_t mjobs_at = place(sizeof(ppf::MixJob) * mjobs.size(), 16);
     const size_t mitems_at = place(sizeof(ppf::MixItem) * mitems.size(), 16);
-    const size_t mfirst_at = place(sizeof(int) * mfirst.size(), 16);
+    const size_t mnext_at = place(sizeof(int) * 4, 16);
     for (size_t gi = 0; gi < order.size(); ++gi) {
         G& g = groups[order[gi]];
         Tab& tb = tabs[gi];
@@ -776,7 +778,7 @@ ppf_status_t ppf_server_tick(ppf_server_t s, void* stream, int* n_done)
     std::memcpy(hs + carry_at, carry.data(), sizeof(CopySeg) * carry.size());
     std::memcpy(hs + mjobs_at, mjobs.data(), sizeof(ppf::MixJob) * mjobs.size());
     std::memcpy(hs + mitems_at, mitems.data(), sizeof(ppf::MixItem) * mitems.size());
-    std::memcpy(hs + mfirst_at, mfirst.data(), sizeof(int) * mfirst.size());
+    std::memset(hs + mnext_at, 0, sizeof(int) * 4);  // the item counter starts from zero
     std::vector<ppf::PpfWork> works(order.size());
     for (size_t gi = 0; gi < order.size(); ++gi) {
         G& g = groups[order[gi]];
@@ -812,7 +814,8 @@ ppf_status_t ppf_server_tick(ppf_server_t s, void* stream, int* n_done)
         ppf::MixWork mw{};
         mw.jobs = reinterpret_cast<const ppf::MixJob*>(ds + mjobs_at);
         mw.items = reinterpret_cast<const ppf::MixItem*>(ds + mitems_at);
-        mw.first = reinterpret_cast<const int*>(ds + mfirst_at);
+        mw.n_items = (int)mitems.size();
+        mw.next = reinterpret_cast<int*>(ds + mnext_at);
         int* err = nullptr;
         for (auto& sl : s->slots)
             if (sl.used && sl.mix) {

@@ -162,9 +162,9 @@ def test_batch_mixes_fp16_and_complex64_outputs(ppf):
         assert torch.equal(yd, ref), (plan.kernel, plan.out_f16)
 
 
-# (N, T) of every tile shape of the mixed-shape kernel (complex64, N*T <= 16K)
+# (N, T) of every tile shape of the mixed-shape kernel (complex64, 128 <= N <= 2048, N*T <= 16K)
 MIX_SHAPES = [(128, 4), (128, 8), (128, 16), (128, 32), (256, 4), (256, 8), (256, 16), (256, 32), (512, 4),
-              (512, 8), (512, 16), (512, 32), (1024, 4), (1024, 8), (1024, 16), (2048, 4), (2048, 8), (4096, 4)]
+              (512, 8), (512, 16), (512, 32), (1024, 4), (1024, 8), (1024, 16), (2048, 4), (2048, 8)]
 
 
 @pytest.mark.parametrize("graph", [False, True])
@@ -178,7 +178,7 @@ def test_batch_mixed_shapes_one_launch(ppf, graph):
     specs = []
     for N, T in MIX_SHAPES:
         specs.append((N, T, "c32", int(g.integers(1, max(3, 24576 // N)))))
-    specs += [(256, 8, "c32", 3001), (1024, 4, "c32", 613), (4096, 4, "c32", 1), (512, 32, "c32", 0)]
+    specs += [(256, 8, "c32", 3001), (1024, 4, "c32", 613), (2048, 4, "c32", 1), (512, 32, "c32", 0)]
     jobs = _jobs(ppf, specs, 9500)
     batch = ppf.Batch(jobs, graph=graph)
     assert batch.launches == 1
@@ -199,6 +199,48 @@ def test_batch_mixed_shapes_one_launch(ppf, graph):
     torch.cuda.synchronize()
     check_oracle(jobs)
     batch.close()
+
+
+def test_batch_mixed_ring_reaches_buffer_slot(ppf):
+    """Streams whose ring reaches into the first FFT buffer slot (512x32,
+    1024x16) alternate with streams whose buffer fills a whole slot (2048x4,
+    512x8, 1024x8), so that CTAs cross from one to the other inside their
+    segment and must wait for the FFT warps first: every spectrum against the
+    oracle and bitwise against ppf_execute."""
+    import torch
+    specs = []
+    for k in range(4):
+        specs += [(2048, 4, "c32", 97 + k), (1024, 16, "c32", 61 + 3 * k), (512, 8, "c32", 203 + k),
+                  (512, 32, "c32", 88 + k), (1024, 8, "c32", 45 + k)]
+    jobs = _jobs(ppf, specs, 9800)
+    batch = ppf.Batch(jobs)
+    assert batch.launches == 1
+    batch.execute()
+    torch.cuda.synchronize()
+    check_oracle(jobs)
+    for plan, xd, yd, S in jobs:
+        assert torch.equal(yd, plan(xd, n_spectra=S)), (plan.N, plan.T, plan.kernel)
+    batch.close()
+
+
+def test_batch_groups_beside_the_mixed_launch(ppf):
+    """Cluster-kernel and 4096-channel jobs in their own group launches after
+    the mixed launch (graph and eager): oracle and bitwise parity."""
+    import torch
+    specs = [(2048, 16, "c32", 150), (4096, 8, "c32", 77), (4096, 4, "c32", 64), (1024, 32, "c32", 90),
+             (2048, 4, "c32", 400), (512, 8, "c32", 900), (256, 16, "c32", 1200), (128, 4, "c32", 3000)]
+    jobs = _jobs(ppf, specs, 9900)
+    for graph in (False, True):
+        batch = ppf.Batch(jobs, graph=graph)
+        assert batch.launches == 1 + len({p.kernel for p, _, _, _ in jobs if p.N * p.T > 16384 or p.N == 4096})
+        for _, _, yd, _ in jobs:
+            yd.fill_(float("nan"))
+        batch.execute()
+        torch.cuda.synchronize()
+        check_oracle(jobs)
+        for plan, xd, yd, S in jobs:
+            assert torch.equal(yd, plan(xd, n_spectra=S)), (plan.N, plan.T, plan.kernel)
+        batch.close()
 
 
 def test_batch_per_kernel_flag(ppf):
