@@ -1,0 +1,41 @@
+// Warp-specialised gather-kernel variants, complex64 input (N*T of 32K and
+// more).  256 FIR threads (FP32 coefficient pairs, packed FMAs) and 256 FFT
+// threads per CTA: at most 128 registers a thread.
+#include "ppf_gws_impl.cuh"
+
+namespace ppf {
+
+template <class In>
+static int variants_impl(int N, int T, int want, KernelEntry* out)
+{
+    int idx = 0;
+    // one FFT buffer (full first-pass padding) or two (halved padding where
+    // needed to fit); one channel pair of the CTA's slice per FIR thread
+    PPF_GWV(4096, 32, 8, 256, 256, 1, 6, 1, 1) PPF_GWV(4096, 32, 8, 256, 256, 1, 5, 2, 2)
+    PPF_GWV(4096, 16, 8, 256, 256, 1, 4, 1, 1) PPF_GWV(4096, 16, 8, 256, 256, 1, 4, 2, 1)
+    PPF_GWV(4096, 8, 4, 256, 256, 1, 4, 1, 1) PPF_GWV(4096, 8, 4, 256, 256, 1, 4, 2, 1)
+    PPF_GWV(2048, 32, 4, 256, 256, 2, 6, 1, 1) PPF_GWV(2048, 32, 4, 256, 256, 2, 5, 2, 2)
+    PPF_GWV(2048, 16, 4, 256, 256, 2, 4, 1, 1) PPF_GWV(2048, 16, 4, 256, 256, 2, 4, 2, 1)
+    PPF_GWV(1024, 32, 2, 256, 256, 4, 6, 1, 1)
+    // four channel pairs per FIR thread at T = 8
+    PPF_GWV(4096, 8, 2, 256, 256, 1, 6, 1, 1)
+    return idx;
+}
+
+int gws_variants_c32(int N, int T, int want, KernelEntry* out)
+{
+    return variants_impl<InC32>(N, T, want, out);
+}
+
+// FP16-output twins (none yet: a plan with FP16 output runs the twin of the
+// gather tile its complex64 counterpart would run, else the general kernel)
+int gws_variants_f16_c32(int N, int T, int want, KernelEntry* out)
+{
+    (void)N;
+    (void)T;
+    (void)want;
+    (void)out;
+    return 0;
+}
+
+}  // namespace ppf

@@ -20,18 +20,23 @@ int gather_variants_ci8(int N, int T, int want, KernelEntry* out);
 int ws_variants_c32(int N, int T, int want, KernelEntry* out);
 int ws_variants_c16(int N, int T, int want, KernelEntry* out);
 int ws_variants_ci8(int N, int T, int want, KernelEntry* out);
+int gws_variants_c32(int N, int T, int want, KernelEntry* out);
+int gws_variants_c16(int N, int T, int want, KernelEntry* out);
+int gws_variants_ci8(int N, int T, int want, KernelEntry* out);
 int ring_variants_f16_c32(int N, int T, int want, KernelEntry* out);
 int gather_variants_f16_c32(int N, int T, int want, KernelEntry* out);
 int ws_variants_f16_c32(int N, int T, int want, KernelEntry* out);
+int gws_variants_f16_c32(int N, int T, int want, KernelEntry* out);
 
 using VariantFn = int (*)(int, int, int, KernelEntry*);
 
 // Number of variants for (N, T, dtype); fills *out with variant `want` if it exists.
 int variants(int N, int T, int dtype, int want, KernelEntry* out)
 {
-    static const VariantFn lists[3][3] = {{ring_variants_c32, gather_variants_c32, ws_variants_c32},
-                                          {ring_variants_c16, gather_variants_c16, ws_variants_c16},
-                                          {ring_variants_ci8, gather_variants_ci8, ws_variants_ci8}};
+    static const VariantFn lists[3][4] = {
+        {ring_variants_c32, gather_variants_c32, ws_variants_c32, gws_variants_c32},
+        {ring_variants_c16, gather_variants_c16, ws_variants_c16, gws_variants_c16},
+        {ring_variants_ci8, gather_variants_ci8, ws_variants_ci8, gws_variants_ci8}};
     if (dtype < 0 || dtype > 2) return 0;
     int n = 0;
     for (VariantFn f : lists[dtype]) {
@@ -80,7 +85,8 @@ static int tuned_variant(int N, int T, int dtype)
 // input only); an empty entry when none is compiled.
 static KernelEntry f16_twin(int N, int T, int dtype, const char* name)
 {
-    static const VariantFn lists[] = {ring_variants_f16_c32, gather_variants_f16_c32, ws_variants_f16_c32};
+    static const VariantFn lists[] = {ring_variants_f16_c32, gather_variants_f16_c32, ws_variants_f16_c32,
+                                      gws_variants_f16_c32};
     if (dtype != 0 || !name) return KernelEntry{};
     char want[112];
     std::snprintf(want, sizeof(want), "%s:f16", name);
