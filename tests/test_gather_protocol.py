@@ -139,3 +139,110 @@ def test_pipelined_rounds_complete_without_overwrites(P, nr, seed):
                 assert progressed or not live, f"deadlock (P={P}, rounds={nr}, trial={trial})"
         for c in ctas:
             assert c.done_rounds == list(range(nr))
+
+
+# --------------------------------------------------------------------------
+# The warp-specialised gather kernel (paper_1411_3656_gb300/csrc/ppf_gws.cuh):
+# every CTA runs two programs at once, a FIR role and an FFT role, over the
+# same rounds.  Round g uses buffer b = g mod NXB (NXB = 1 or 2 FFT buffers per
+# CTA), phase g // NXB of that buffer's barriers.  The FIR role filters round g,
+# then (g >= NXB) waits for phase (g - NXB) // NXB of its "free" barrier of b,
+# only then makes the local arrival (expected bytes) on its own "full" barrier
+# of b, and stores its slice into every owner's buffer b.  The FFT role waits
+# for phase g // NXB of its "full" barrier of b, reads the buffer, arrives on
+# every CTA's "free" barrier of b and stores the spectra.  The FIR role may run
+# ahead of its own FFT role; the model checks that the local arrival never
+# lands on a phase that has not completed yet.
+
+
+def gws_programs(me, ctas, nr, nxb, arrive_before_free_wait=False, skip_free_wait=False):
+    P = len(ctas)
+
+    def fir_role():
+        for g in range(nr):
+            b = g % nxb
+            yield None  # the FIR arithmetic of round g
+            if arrive_before_free_wait:
+                me.full[b].arrive()
+            if g >= nxb and not skip_free_wait:
+                while not me.free[b].wait_ready((g - nxb) // nxb):
+                    yield "wait"
+            if not arrive_before_free_wait:
+                # the earlier phase of this buffer has completed
+                assert me.full[b].completed == g // nxb, "local arrival on a phase still open"
+                me.full[b].arrive()
+            for owner in ctas:
+                assert owner.reading[b] != g - nxb, "slice stored into a buffer still being read"
+                assert owner.full[b].completed == g // nxb, "slice of round g counted in another phase"
+                owner.buf[b][me.rank] = g
+                owner.full[b].complete_tx()
+                yield None
+
+    def fft_role():
+        for g in range(nr):
+            b = g % nxb
+            while not me.full[b].wait_ready(g // nxb):
+                yield "wait"
+            assert me.buf[b] == {r: g for r in range(P)}, "FFT input is not exactly round g's slices"
+            me.reading[b] = g
+            yield None  # the passes' loads
+            me.reading[b] = None
+            for peer in ctas:
+                peer.free[b].arrive()
+            yield None  # the rest of the passes and the stores
+            me.done_rounds.append(g)
+
+    return fir_role(), fft_role()
+
+
+def run_gws_model(P, nr, nxb, seed, trials=40, **mistake):
+    rng = random.Random(seed)
+    for trial in range(trials):
+        ctas = [CTA(r, P) for r in range(P)]
+        progs = {}
+        for r in range(P):
+            progs[(r, "fir")], progs[(r, "fft")] = gws_programs(ctas[r], ctas, nr, nxb, **mistake)
+        blocked = {k: False for k in progs}
+        live = set(progs)
+        steps = 0
+        while live:
+            steps += 1
+            assert steps < 200000
+            k = rng.choice(sorted(live))
+            try:
+                st = next(progs[k])
+            except StopIteration:
+                live.discard(k)
+                continue
+            blocked[k] = st == "wait"
+            if live and all(blocked[q] for q in live):
+                progressed = False
+                for q in sorted(live):
+                    try:
+                        st = next(progs[q])
+                    except StopIteration:
+                        live.discard(q)
+                        progressed = True
+                        continue
+                    if st != "wait":
+                        blocked[q] = False
+                        progressed = True
+                assert progressed or not live, f"deadlock (P={P}, rounds={nr}, NXB={nxb}, trial={trial})"
+        for c in ctas:
+            assert c.done_rounds == list(range(nr))
+
+
+@pytest.mark.parametrize("nxb", [1, 2])
+@pytest.mark.parametrize("P,nr,seed", [(2, 1, 10), (2, 7, 11), (4, 9, 12), (8, 12, 13), (3, 10, 14)])
+def test_warp_specialised_rounds_complete_without_overwrites(P, nr, nxb, seed):
+    run_gws_model(P, nr, nxb, seed)
+
+
+@pytest.mark.parametrize("mistake", ["arrive_before_free_wait", "skip_free_wait"])
+@pytest.mark.parametrize("nxb", [1, 2])
+def test_warp_specialised_planted_mistakes_fail(mistake, nxb):
+    """The local arrival made before the wait for the buffer's release, or the
+    release wait left out, is caught in some interleaving."""
+    with pytest.raises(AssertionError):
+        for seed in range(30):
+            run_gws_model(4, 8, nxb, 100 + seed, trials=20, **{mistake: True})
