@@ -27,15 +27,18 @@ int gws_variants_c32(int N, int T, int want, KernelEntry* out)
     return variants_impl<InC32>(N, T, want, out);
 }
 
-// FP16-output twins (none yet: a plan with FP16 output runs the twin of the
-// gather tile its complex64 counterpart would run, else the general kernel)
+// FP16-output twins of the tuned tile shapes (complex64 input).
+template <class In>
+static int variants_f16_impl(int N, int T, int want, KernelEntry* out)
+{
+    int idx = 0;
+    PPF_GWVF(4096, 8, 4, 256, 256, 1, 4, 2, 1) PPF_GWVF(1024, 32, 2, 256, 256, 4, 6, 1, 1)
+    return idx;
+}
+
 int gws_variants_f16_c32(int N, int T, int want, KernelEntry* out)
 {
-    (void)N;
-    (void)T;
-    (void)want;
-    (void)out;
-    return 0;
+    return variants_f16_impl<InC32>(N, T, want, out);
 }
 
 }  // namespace ppf
