@@ -224,10 +224,11 @@ ppf_status_t ppf_execute_noalloc(int N, int T, ppf_dtype_t dtype, const float* d
  * dtype and coefficients) in as few launches as possible.  This is the
  * method's data-parallel form over streams (Section 3 processes one stream;
  * independent streams simply run side by side).  Every complex64 job whose
- * (N, T) has a tile shape in the mixed-shape kernel (N >= 128 and
+ * (N, T) has a tile shape in the mixed-shape kernel (128 <= N <= 2048 and
  * N*T <= 16384, complex64 output, the plan's tuned default) joins ONE
  * persistent launch over a device work list of (job, spectrum band) items of
- * any N and T, which the CTAs take largest first as they become free.  Other
+ * any N and T and about equal measured cost, which the CTAs take largest
+ * first, each CTA asking for the next item when it has finished one.  Other
  * jobs whose plans use the same specialised kernel share one persistent
  * launch over their work list; jobs on the general kernel launch one by one.
  */
@@ -255,7 +256,9 @@ typedef struct {
 ppf_status_t ppf_batch_create(ppf_batch_t* out, const ppf_job_t* jobs, int n_jobs, unsigned flags);
 
 /* Enqueue every job of the batch on `stream` (cudaStream_t as void*), as a
- * CUDA graph launch when the batch was created with PPF_BATCH_GRAPH. */
+ * CUDA graph launch when the batch was created with PPF_BATCH_GRAPH.  An
+ * execution first zeroes the batch's device item counter: two executions of
+ * one batch must not overlap on the GPU (order them on one stream). */
 ppf_status_t ppf_batch_execute(ppf_batch_t batch, void* stream);
 
 /* Kernel launches one execution enqueues (1 for a captured graph counts its

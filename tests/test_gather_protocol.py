@@ -63,7 +63,7 @@ class CTA:
         self.done_rounds = []
 
 
-def cta_program(me, ctas, nr):
+def cta_program(me, ctas, nr, skip_free_wait=False, free_before_read=False):
     P = len(ctas)
 
     def fir(g):
@@ -72,7 +72,7 @@ def cta_program(me, ctas, nr):
         assert me.full[b].completed == g >> 1
         me.full[b].arrive()
         yield None  # the FIR arithmetic
-        if g >= 2:
+        if g >= 2 and not skip_free_wait:
             while not me.free[b].wait_ready((g - 2) >> 1):
                 yield "wait"
         for owner in ctas:
@@ -87,12 +87,17 @@ def cta_program(me, ctas, nr):
         b = g & 1
         while not me.full[b].wait_ready(g >> 1):
             yield "wait"
+        if free_before_read:
+            for peer in ctas:
+                peer.free[b].arrive()
+            yield None
         assert me.buf[b] == {r: g for r in range(P)}, "FFT input is not exactly round g's slices"
         me.reading[b] = g
         yield None  # the passes' loads
         me.reading[b] = None
-        for peer in ctas:
-            peer.free[b].arrive()
+        if not free_before_read:
+            for peer in ctas:
+                peer.free[b].arrive()
         yield None  # the rest of the passes and the stores
         me.done_rounds.append(g)
 
@@ -106,10 +111,23 @@ def cta_program(me, ctas, nr):
 
 @pytest.mark.parametrize("P,nr,seed", [(2, 1, 0), (2, 2, 1), (2, 9, 2), (4, 7, 3), (8, 12, 4), (8, 3, 5), (3, 10, 6)])
 def test_pipelined_rounds_complete_without_overwrites(P, nr, seed):
+    run_gather_model(P, nr, seed)
+
+
+@pytest.mark.parametrize("mistake", ["skip_free_wait", "free_before_read"])
+def test_pipelined_planted_mistakes_fail(mistake):
+    """The sender's wait for the buffer's release left out, or an owner freeing a
+    buffer before reading it, is caught in some interleaving."""
+    with pytest.raises(AssertionError):
+        for seed in range(30):
+            run_gather_model(4, 8, 200 + seed, trials=20, **{mistake: True})
+
+
+def run_gather_model(P, nr, seed, trials=40, **mistake):
     rng = random.Random(seed)
-    for trial in range(40):
+    for trial in range(trials):
         ctas = [CTA(r, P) for r in range(P)]
-        progs = {r: cta_program(ctas[r], ctas, nr) for r in range(P)}
+        progs = {r: cta_program(ctas[r], ctas, nr, **mistake) for r in range(P)}
         blocked = {r: False for r in range(P)}
         live = set(range(P))
         steps = 0
