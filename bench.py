@@ -52,6 +52,7 @@ def parse():
     ap.add_argument("--serve-default", default="128,256",
                     help="default run: stream counts of the serving sub-object (each held --serve-seconds)")
     ap.add_argument("--no-serving", action="store_true", help="default run: skip the serving sub-object")
+    ap.add_argument("--no-batched", action="store_true", help="default run: skip the batched-streams sub-object")
     ap.add_argument("--no-precision", action="store_true",
                     help="default run: skip the FP16 / int8 input sweeps of the precision sub-object")
     ap.add_argument("--cells", default="", help="comma list N:T to restrict the sweep")
@@ -638,6 +639,16 @@ def run_ours(args):
     if rank == 0 and world == 1 and not args.no_serving and args.workload == "realtime_sweep":
         serving_obj = serving_summary(args)
 
+    batched_obj = None
+    if rank == 0 and world == 1 and not args.no_batched and args.workload == "realtime_sweep":
+        try:
+            b = batched_measure(args)
+            batched_obj = {k: b[k] for k in ("metric", "value", "unit", "ms_per_step", "one_launch_per_stream",
+                                             "one_launch_per_kernel", "batch_launches_per_step", "roofline")}
+            batched_obj["workload"] = b["config"]["workload"]
+        except Exception as e:  # a sub-object: report, do not fail the bench
+            batched_obj = {"error": f"{type(e).__name__}: {e}"[:200]}
+
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         v, cores, desc = oracle_baseline(args, cells, x_host, args.cpu_seconds)
@@ -669,6 +680,7 @@ def run_ours(args):
             "unfused": unfused,
             "precision": precision,
             "serving": serving_obj,
+            "batched": batched_obj,
             "cells": cell_rows,
         }
         print(json.dumps(line), flush=True)
@@ -700,6 +712,13 @@ def batched_streams(n=64, seed=1411_3656 + 4):
 
 def run_batched(args):
     """Batched uneven streams: one graph-captured batch vs one launch per stream."""
+    print(json.dumps(batched_measure(args)), flush=True)
+    return 0
+
+
+def batched_measure(args):
+    """The batched-streams line: one graph-captured batch vs one launch per stream
+    and one launch per kernel, on the same 64 streams."""
     import torch
     from paper_1411_3656_gb300 import build, metrics, ppf, synth
     build.build()
@@ -769,10 +788,11 @@ def run_batched(args):
         # library's launch counter: count them from the batch
         "gpu_launches": launches if launches > 0 else batch.launches * args.steps, "clocks": clock,
     }
-    print(json.dumps(line), flush=True)
     batch.close()
     per_kernel.close()
-    return 0
+    for plan, _, _, _ in jobs:
+        plan.close()
+    return line
 
 
 def run_serving(args):
