@@ -38,7 +38,7 @@
 namespace ppf {
 
 template <int N_, int T_, class In_, int P_, int NF_, int NX_, int RB_, int NCH_, int NXB_ = 1, class OT_ = float2,
-          int PD_ = 1>
+          int PD_ = 1, int RF_ = 0, int RX_ = 0, int ER_ = 0>
 struct GwsCfg {
     using OT = OT_;  // output bin: float2 (complex64) or BinF16
     using In = In_;
@@ -54,6 +54,11 @@ struct GwsCfg {
     static constexpr int RG = UNITS >= NF ? 1 : NF / UNITS;
     static constexpr int RBT = ROWS / RG;                // spectra per FIR thread per round
     static constexpr int KO = T >= 2 ? (T - 2) / ROWS + 1 : 0;
+    // early refill (ER, one row group whose window runs past its first
+    // chunk): chunks are waited for as the window reaches them and the first
+    // is refilled mid-round, at the cost of a second FIR barrier per round
+    static constexpr bool EARLY = ER_ != 0 && RG == 1 && RBT + T - 1 > ROWS;
+    static_assert(ER_ == 0 || EARLY, "early refill needs one row group and a window past its first chunk");
     static constexpr int RING_ROWS = NCH * ROWS;
     static constexpr int SEG_BYTES = NC * BPS;           // one input row's slice
     static constexpr int CHUNK_BYTES = ROWS * SEG_BYTES;
@@ -62,6 +67,18 @@ struct GwsCfg {
     static constexpr int X_SLOTS = RB * RS;              // one FFT buffer
     static constexpr int XBYTES = RB * N * 8;            // bytes a buffer receives per round
     static constexpr int SMEM = RING_BYTES + NXB * X_SLOTS * 8 + (NCH + 2 * NXB) * 8;
+    // Register split (RF > 0): at launch every thread gets the same count
+    // (LREG, the launch bound's share of the 64K-register file); the FIR
+    // warpgroups then raise theirs to RF and the FFT warpgroups lower theirs
+    // to RX, so the FIR's coefficients and accumulators need not spill to fit
+    // the FFT threads' count.  The host refuses the tile if the compiled
+    // kernel was given fewer than LREG registers a thread at launch.
+    static constexpr int RF = RF_, RX = RX_;
+    static constexpr int LREG = (65536 / NT) / 8 * 8 > 255 ? 255 : (65536 / NT) / 8 * 8;
+    static_assert(RF == 0 || (NF % 128 == 0 && NX % 128 == 0), "register split: whole warpgroups per role");
+    static_assert(RF == 0 || (RF % 8 == 0 && RX % 8 == 0 && RX >= 24 && RF <= 256),
+                  "register split: FIR count up, FFT count down, multiples of 8");
+    static_assert(RF == 0 || NF * RF + NX * RX <= NT * LREG, "register split exceeds the launch pool");
     static_assert(P >= 2 && P <= 8, "portable cluster sizes");
     static_assert(N % (2 * P) == 0 && SEG_BYTES % 16 == 0, "16-byte row slices");
     static_assert(NF % 32 == 0 && NX % 32 == 0 && NT <= 1024, "whole warps per role");
@@ -184,12 +201,9 @@ __device__ __forceinline__ void gws_fir_role(const PpfWork& wl, unsigned char* r
         }
 
         int waited = 0;
-        for (int k = 0; k < nr; ++k) {
-            const int gk = gbase + k;
-            const int b = gws_buf<C>(gk);
-            const int rrb = ((cbase + k) % NCH) * ROWS;
-            // 1. the round needs chunks k .. k+KO; every thread waits itself
-            const int need = (k + C::KO < nchunks ? k + C::KO : nchunks - 1) + 1;
+        // every thread waits itself for the item's chunks up to `upto`
+        auto wait_chunks = [&](int upto) {
+            const int need = (upto < nchunks ? upto : nchunks - 1) + 1;
             for (; waited < need && !failed; ++waited) {
                 const int gc = cbase + waited;
                 if (!mbar_wait_bounded(&bars[gc % NCH], (uint32_t)((gc / NCH) & 1))) {
@@ -197,6 +211,28 @@ __device__ __forceinline__ void gws_fir_role(const PpfWork& wl, unsigned char* r
                     break;  // this chunk stays "not waited for": the drain below waits for it
                 }
             }
+        };
+        // once every FIR thread is past the round's first chunk, its slot
+        // takes the next chunk of the item (in order)
+        auto refill = [&](int k) {
+            failed = nbar_sync_or(kBarFir, NF, failed);
+            if (tid == 0 && !failed && issued < nchunks && issued == k + NCH) {
+                issue(issued);
+                ++issued;
+            }
+        };
+        for (int k = 0; k < nr; ++k) {
+            const int gk = gbase + k;
+            const int b = gws_buf<C>(gk);
+            const int rrb = ((cbase + k) % NCH) * ROWS;
+            // 1. the round reads chunks k .. k+KO.  With one row group (every
+            //    thread filters all of the round's spectra) each chunk is
+            //    waited for right before the window first reaches it, and the
+            //    first chunk's slot is refilled as soon as every thread has
+            //    passed it (EARLY), so a refill has more than a round to land;
+            //    otherwise all are waited for here and the refill follows the
+            //    round.
+            if constexpr (!C::EARLY) wait_chunks(k + C::KO);
             // 2. FIR over the ring; row i of the round goes to CTA i / RB.
             //    With one row group the window starts at a chunk boundary, so
             //    the chunk bases are computed once per round.
@@ -231,6 +267,10 @@ __device__ __forceinline__ void gws_fir_role(const PpfWork& wl, unsigned char* r
                 }
 #pragma unroll
                 for (int u = 0; u < RBT + T - 1; ++u) {
+                    if constexpr (C::EARLY) {
+                        if (g == 0 && u % ROWS == 0) wait_chunks(k + u / ROWS);
+                        if (g == G - 1 && u == ROWS) refill(k);
+                    }
                     const size_t ro = ring_off(u, cl);
                     const PV pv = PPF_INBOUNDS(ro + sizeof(PV) <= (size_t)C::RING_BYTES)
                                       ? *reinterpret_cast<const PV*>(ring + ro)
@@ -281,11 +321,7 @@ __device__ __forceinline__ void gws_fir_role(const PpfWork& wl, unsigned char* r
                 }
             }
             // 4. every FIR thread's reads of chunk k are done: refill its slot
-            failed = nbar_sync_or(kBarFir, NF, failed);
-            if (tid == 0 && !failed && issued < nchunks && issued == k + NCH) {
-                issue(issued);
-                ++issued;
-            }
+            if constexpr (!C::EARLY) refill(k);
         }
         if (failed && tid == 0) {
             // let the copies still in flight land before the CTA moves on or exits
@@ -368,10 +404,13 @@ ppf_gws_kernel(const PpfWork wl, const float2* __restrict__ tw, int* __restrict_
     bool failed = false;
     // warps 0 .. NF/32-1 filter, the others transform (role boundaries fall
     // on warp boundaries, so every named barrier is executed warp-uniformly)
-    if (threadIdx.x < C::NF)
+    if (threadIdx.x < C::NF) {
+        if constexpr (C::RF > 0) regs_inc<C::RF>();
         gws_fir_role<C>(wl, ring, smem_u32(X), bars, xfull, xfree, rank, cid, ncl, failed);
-    else
+    } else {
+        if constexpr (C::RF > 0) regs_dec<C::RX>();
         gws_fft_role<C>(wl, X, tw, xfull, xfree, rank, cid, ncl, failed);
+    }
     const bool any_failed = __syncthreads_or(failed);
     // no CTA leaves while a peer may still store into its shared memory
     cluster_arrive_release();

@@ -19,6 +19,13 @@ static int variants_impl(int N, int T, int want, KernelEntry* out)
     PPF_GWV(1024, 32, 2, 256, 256, 4, 6, 1, 1)
     // four channel pairs per FIR thread at T = 8
     PPF_GWV(4096, 8, 2, 256, 256, 1, 6, 1, 1)
+    // register splits (T = 32): each role allocated on its own (128/128),
+    // or the FIR warpgroups raised above the launch share
+    PPF_GWVR(4096, 32, 8, 256, 256, 1, 6, 1, 1, 128, 128, 0) PPF_GWVR(4096, 32, 8, 256, 256, 1, 6, 1, 1, 136, 120, 0)
+    PPF_GWVR(2048, 32, 4, 256, 256, 2, 6, 1, 1, 128, 128, 0) PPF_GWVR(1024, 32, 2, 256, 256, 4, 6, 1, 1, 128, 128, 0)
+    // early ring refill
+    PPF_GWVR(4096, 8, 4, 256, 256, 1, 4, 2, 1, 0, 0, 1) PPF_GWVR(4096, 16, 8, 256, 256, 1, 4, 2, 1, 0, 0, 1)
+    PPF_GWVR(2048, 16, 4, 256, 256, 2, 4, 2, 1, 0, 0, 1)
     return idx;
 }
 

@@ -3,6 +3,7 @@
 #pragma once
 
 #include <cstdio>
+#include <cstring>
 #include <type_traits>
 
 #include "ppf_gws.cuh"
@@ -33,6 +34,16 @@ cudaError_t prepare_gws(PlanView& p)
 {
     cudaError_t e = cudaFuncSetAttribute(ppf_gws_kernel<C>, cudaFuncAttributeMaxDynamicSharedMemorySize, C::SMEM);
     if (e != cudaSuccess) return e;
+    if constexpr (C::RF > 0) {
+        // the register split draws on the launch pool: the kernel must have
+        // been compiled with the full share, or the FIR warps' request
+        // could never be granted
+        cudaFuncAttributes fa;
+        e = cudaFuncGetAttributes(&fa, ppf_gws_kernel<C>);
+        if (e != cudaSuccess) return e;
+        if ((long)fa.numRegs * C::NT < (long)C::NF * C::RF + (long)C::NX * C::RX)
+            return cudaErrorInvalidConfiguration;
+    }
     cudaLaunchAttribute attr[1];
     cudaLaunchConfig_t cfg = launch_config<C>(C::P * p.sms, nullptr, attr);
     int ncl = 0;
@@ -79,8 +90,11 @@ template <class C>
 KernelEntry entry()
 {
     static char name[96];
-    std::snprintf(name, sizeof(name), "gws:p%d:nf%d:nx%d:rb%d:nch%d%s%s%s", C::P, C::NF, C::NX, C::RB, C::NCH,
-                  C::NXB == 2 ? ":db" : "", C::PD == 2 ? ":pd2" : "",
+    char split[24] = "";
+    if (C::RF > 0) std::snprintf(split, sizeof(split), ":r%d/%d", C::RF, C::RX);
+    if (C::EARLY) std::snprintf(split + std::strlen(split), sizeof(split) - std::strlen(split), ":er");
+    std::snprintf(name, sizeof(name), "gws:p%d:nf%d:nx%d:rb%d:nch%d%s%s%s%s", C::P, C::NF, C::NX, C::RB, C::NCH,
+                  C::NXB == 2 ? ":db" : "", C::PD == 2 ? ":pd2" : "", split,
                   std::is_same<typename C::OT, BinF16>::value ? ":f16" : "");
     KernelEntry e;
     e.name = name;
@@ -102,6 +116,15 @@ KernelEntry entry()
     if (N == NN && T == TT) {                                                                            \
         if (idx == want && out)                                                                          \
             *out = gws_detail::entry<GwsCfg<NN, TT, In, P, NF, NX, RB, NCH, NXB, float2, PD>>();         \
+        ++idx;                                                                                           \
+    }
+// PPF_GWVR: the same with a register split, FIR warpgroups at RF registers a
+// thread and FFT warpgroups at RX (RF = 0: none), and the early ring refill
+// when ER is 1.
+#define PPF_GWVR(NN, TT, P, NF, NX, RB, NCH, NXB, PD, RF, RX, ER)                                        \
+    if (N == NN && T == TT) {                                                                            \
+        if (idx == want && out)                                                                          \
+            *out = gws_detail::entry<GwsCfg<NN, TT, In, P, NF, NX, RB, NCH, NXB, float2, PD, RF, RX, ER>>(); \
         ++idx;                                                                                           \
     }
 #define PPF_GWVF(NN, TT, P, NF, NX, RB, NCH, NXB, PD)                                                    \

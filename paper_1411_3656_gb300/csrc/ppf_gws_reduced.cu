@@ -15,6 +15,9 @@ static int variants_impl(int N, int T, int want, KernelEntry* out)
     PPF_GWV(1024, 32, 2, 256, 256, 4, 6, 1, 1) PPF_GWV(1024, 32, 2, 256, 256, 4, 6, 2, 1)
     PPF_GWV(2048, 16, 2, 256, 256, 2, 6, 2, 1) PPF_GWV(2048, 16, 4, 256, 256, 2, 4, 2, 1)
     PPF_GWV(4096, 8, 2, 256, 256, 1, 6, 2, 1) PPF_GWV(4096, 8, 4, 256, 256, 1, 4, 2, 1)
+    // early ring refill
+    PPF_GWVR(4096, 8, 2, 256, 256, 1, 6, 2, 1, 0, 0, 1) PPF_GWVR(4096, 8, 4, 256, 256, 1, 4, 2, 1, 0, 0, 1)
+    PPF_GWVR(2048, 16, 2, 256, 256, 2, 6, 2, 1, 0, 0, 1) PPF_GWVR(4096, 16, 4, 256, 256, 1, 6, 1, 1, 0, 0, 1)
     return idx;
 }
 

@@ -183,4 +183,24 @@ __device__ __forceinline__ bool nbar_sync_or(int id, int count, bool v)
     return r != 0;
 }
 
+// ---------------------------------------------------------------- register split
+// Move registers between the warpgroups of a CTA (sm_90a and later "a"
+// targets): every thread of a warpgroup executes the same instruction; `dec`
+// hands registers back to the CTA's pool, `inc` waits until the pool holds
+// enough.  The pool is what the CTA was launched with (threads x registers a
+// thread at launch), so the counts a kernel asks for must add up to at most
+// that: the host checks the launch register count before the first launch.
+template <int R>
+__device__ __forceinline__ void regs_inc()
+{
+    static_assert(R >= 24 && R <= 256 && R % 8 == 0, "register count");
+    asm volatile("setmaxnreg.inc.sync.aligned.u32 %0;\n" ::"n"(R));
+}
+template <int R>
+__device__ __forceinline__ void regs_dec()
+{
+    static_assert(R >= 24 && R <= 256 && R % 8 == 0, "register count");
+    asm volatile("setmaxnreg.dec.sync.aligned.u32 %0;\n" ::"n"(R));
+}
+
 }  // namespace ppf
