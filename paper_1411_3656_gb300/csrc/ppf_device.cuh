@@ -118,9 +118,33 @@ __device__ __forceinline__ float2 mul_w16(int m, float2 a)
     return neg ? make_float2(-r.x, -r.y) : r;
 }
 
-// In-register forward DFT of R points (R = 1, 2, 4, 8, 16), natural order in
-// and out: v[k] <- sum_r v[r] * W_R^{r*k}.  Radix-2 decimation in time over
-// compile-time indices; the even/odd copies are register renames.
+// a * W_32^m with W_32 = exp(-2*pi*i/32), m a compile-time constant: even m
+// is W_16^(m/2); odd m is W_32^r (r = 1, 3, 5, 7: cos and sin of r*pi/16, the
+// pairs of r and 8 - r swapped) turned by m / 8 quarter turns (-i each).
+#define PPF_C16 0.98078528040323044913f  // cos(pi/16)
+#define PPF_S16 0.19509032201612826785f  // sin(pi/16)
+#define PPF_C316 0.83146961230254523708f  // cos(3*pi/16)
+#define PPF_S316 0.55557023301960222474f  // sin(3*pi/16)
+__device__ __forceinline__ float2 mul_w32(int m, float2 a)
+{
+    m &= 31;
+    if ((m & 1) == 0) return mul_w16(m >> 1, a);
+    const int q = m >> 3, r = m & 7;
+    float c, sn;  // W_32^r = c - i*sn
+    switch (r) {
+    case 1: c = PPF_C16; sn = PPF_S16; break;
+    case 3: c = PPF_C316; sn = PPF_S316; break;
+    case 5: c = PPF_S316; sn = PPF_C316; break;
+    default: c = PPF_S16; sn = PPF_C16; break;
+    }
+    float2 t = make_float2(fmaf(a.x, c, a.y * sn), fmaf(a.y, c, -a.x * sn));
+    for (int i = 0; i < q; ++i) t = make_float2(t.y, -t.x);
+    return t;
+}
+
+// In-register forward DFT of R points (R = 1, 2, 4, 8, 16, 32), natural order
+// in and out: v[k] <- sum_r v[r] * W_R^{r*k}.  Radix-2 decimation in time
+// over compile-time indices; the even/odd copies are register renames.
 template <int R>
 __device__ __forceinline__ void dft(float2 (&v)[R])
 {
@@ -138,7 +162,7 @@ __device__ __forceinline__ void dft(float2 (&v)[R])
         v[1] = cadd(t1, t3);
         v[3] = csub(t1, t3);
     } else {
-        static_assert(R == 8 || R == 16, "radix must be 1, 2, 4, 8 or 16");
+        static_assert(R == 8 || R == 16 || R == 32, "radix must be 1, 2, 4, 8, 16 or 32");
         float2 e[R / 2], o[R / 2];
 #pragma unroll
         for (int i = 0; i < R / 2; ++i) {
@@ -149,7 +173,7 @@ __device__ __forceinline__ void dft(float2 (&v)[R])
         dft<R / 2>(o);
 #pragma unroll
         for (int k = 0; k < R / 2; ++k) {
-            const float2 t = mul_w16(k * (16 / R), o[k]);
+            const float2 t = R == 32 ? mul_w32(k, o[k]) : mul_w16(k * (16 / R), o[k]);
             v[k] = cadd(e[k], t);
             v[k + R / 2] = csub(e[k], t);
         }
@@ -326,29 +350,30 @@ __host__ __device__ constexpr int fft_ns(int N, int pass)
     return ns;
 }
 
-// The same plan with the first pass's radix capped at R0 (8 or 16), then 16s,
-// the remainder last: 64 = 8 x 8, 32 = 8 x 4, 128 = 8 x 16 for R0 = 8.
-// R0 = 16 gives the plan above.
-__host__ __device__ constexpr int fft_radix_r(int N, int pass, int R0)
+// The same plan with the first pass's radix capped at R0 (8, 16 or 32), the
+// later passes' at RC (16 or 32), the remainder last: 64 = 8 x 8, 32 = 8 x 4,
+// 128 = 8 x 16 for R0 = 8; 1024 = 32 x 32 and 512 = 32 x 16 for R0 = RC = 32.
+// R0 = RC = 16 gives the plan above.
+__host__ __device__ constexpr int fft_radix_r(int N, int pass, int R0, int RC = 16)
 {
     int n = N;
     for (int p = 0;; ++p) {
-        const int cap = p == 0 ? R0 : 16;
+        const int cap = p == 0 ? R0 : RC;
         const int r = n >= cap ? cap : n;
         if (p == pass) return r;
         n /= r;
     }
 }
-__host__ __device__ constexpr int fft_npass_r(int N, int R0)
+__host__ __device__ constexpr int fft_npass_r(int N, int R0, int RC = 16)
 {
     int p = 0;
-    for (int n = N; n > 1; ++p) n /= fft_radix_r(N, p, R0);
+    for (int n = N; n > 1; ++p) n /= fft_radix_r(N, p, R0, RC);
     return p;
 }
-__host__ __device__ constexpr int fft_ns_r(int N, int pass, int R0)
+__host__ __device__ constexpr int fft_ns_r(int N, int pass, int R0, int RC = 16)
 {
     int ns = 1;
-    for (int p = 0; p < pass; ++p) ns *= fft_radix_r(N, p, R0);
+    for (int p = 0; p < pass; ++p) ns *= fft_radix_r(N, p, R0, RC);
     return ns;
 }
 

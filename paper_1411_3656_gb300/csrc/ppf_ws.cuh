@@ -34,18 +34,23 @@ namespace ppf {
 enum : int { kBarFir = 1, kBarFft = 2, kBarFull0 = 3, kBarEmpty0 = 5 };
 
 template <int N_, int T_, class In_, int NF_, int NX_, int RB_, int NCH_, int CPT_ = 2, class OT_ = float2,
-          int PD_ = 1>
+          int PD_ = 1, int RC_ = 16>
 struct WsCfg {
     using OT = OT_;  // output bin: float2 (complex64) or BinF16
     using In = In_;
     using raw = typename In::raw;
     using coef_t = typename Coef<In>::type;
     static constexpr int N = N_, T = T_, NF = NF_, NX = NX_, RB = RB_, NCH = NCH_, CPT = CPT_, PD = PD_;
+    // FFT passes of radix up to RC: 16, or 32 (1024 = 32 x 32, 512 = 32 x 16:
+    // two passes instead of three, one shared-memory round trip less)
+    static constexpr int RC = RC_;
     static constexpr int NT = NF + NX;
     static constexpr int BPS = In::bytes;
     // FFT buffer row stride: room for the first pass's padding (one slot per
-    // 16 elements, or per 32 with PD = 2)
-    static constexpr int RS = PD == 1 ? fft_row_stride(N) : N + (N / 32 > 2 ? N / 32 : 2);
+    // RC elements, or per 2*RC with PD = 2)
+    static constexpr int RS = N + (N / (RC * PD) > 2 ? N / (RC * PD) : 2);
+    static_assert(RC == 16 || RC == 32, "pass radix cap 16 or 32");
+    static_assert(RC == 16 || fft_radix_r(N, 0, RC, RC) == 32, "radix-32 plans start with a radix-32 pass");
     static constexpr int UNITS = N / CPT;                     // FIR work units per row
     static constexpr int G = UNITS > NF ? UNITS / NF : 1;     // units per FIR thread
     static constexpr int RG = UNITS >= NF ? 1 : NF / UNITS;   // row groups
@@ -72,15 +77,15 @@ struct WsCfg {
 // takes in every block: butterfly lt + k*NX of a pass has j = (lt + k*NX) mod
 // N/R, which cycles through J = max(1, (N/R)/NX) values, so J sets of R-1
 // twiddles per pass are loaded once into registers.
-template <int N, int NX, int R0 = 16, int P = 1, bool ANY = (P < fft_npass_r(N, R0))>
+template <int N, int NX, int RC = 16, int P = 1, bool ANY = (P < fft_npass_r(N, RC, RC))>
 struct WsTwiddles {
-    static constexpr int R = fft_radix_r(N, P, R0);
-    static constexpr int NS = fft_ns_r(N, P, R0);
+    static constexpr int R = fft_radix_r(N, P, RC, RC);
+    static constexpr int NS = fft_ns_r(N, P, RC, RC);
     static constexpr int BPR = N / R;
     static constexpr int J = NX >= BPR ? 1 : BPR / NX;
     static_assert(NX % BPR == 0 || BPR % NX == 0, "FFT threads must tile the butterflies of a row");
     float2 w[J][R - 1];
-    WsTwiddles<N, NX, R0, P + 1> next;
+    WsTwiddles<N, NX, RC, P + 1> next;
     __device__ __forceinline__ void load(const float2* __restrict__ tw, int lt)
     {
         constexpr int step = N / (NS * R);
@@ -99,8 +104,8 @@ struct WsTwiddles {
         else return next.template get<Q>(q);
     }
 };
-template <int N, int NX, int R0, int P>
-struct WsTwiddles<N, NX, R0, P, false> {
+template <int N, int NX, int RC, int P>
+struct WsTwiddles<N, NX, RC, P, false> {
     __device__ __forceinline__ void load(const float2* __restrict__, int) {}
     template <int Q>
     __device__ __forceinline__ const float2* get(int) const { return nullptr; }
@@ -110,15 +115,15 @@ struct WsTwiddles<N, NX, R0, P, false> {
 // (role index lt): loads, FFT barrier, then twiddles, DFT and stores (the last
 // pass stores the spectra to global memory and does not touch `buf` again,
 // so it needs no barrier; `after_last_read` runs right after its loads).
-template <int N, int RB, int NX, int RS, int PD, int P, class OT, class F>
-__device__ __forceinline__ void ws_fft_pass(float2* buf, const WsTwiddles<N, NX>& tw, OT* __restrict__ Yb, int rows,
-                                            int lt, F&& after_last_read)
+template <int N, int RB, int NX, int RS, int PD, int RC, int P, class OT, class F>
+__device__ __forceinline__ void ws_fft_pass(float2* buf, const WsTwiddles<N, NX, RC>& tw, OT* __restrict__ Yb,
+                                            int rows, int lt, F&& after_last_read)
 {
-    constexpr int R = fft_radix(N, P);
-    constexpr int NS = fft_ns(N, P);
-    constexpr bool LAST = (P == fft_npass(N) - 1);
-    constexpr int IN_NS = P == 0 ? 0 : fft_ns(N, P - 1);
-    constexpr int IN_R = P == 0 ? 1 : fft_radix(N, P - 1);
+    constexpr int R = fft_radix_r(N, P, RC, RC);
+    constexpr int NS = fft_ns_r(N, P, RC, RC);
+    constexpr bool LAST = (P == fft_npass_r(N, RC, RC) - 1);
+    constexpr int IN_NS = P == 0 ? 0 : fft_ns_r(N, P - 1, RC, RC);
+    constexpr int IN_R = P == 0 ? 1 : fft_radix_r(N, P - 1, RC, RC);
     constexpr int BPR = N / R;
     constexpr int NB = RB * BPR;
     constexpr int PER = (NB + NX - 1) / NX;
@@ -163,13 +168,13 @@ __device__ __forceinline__ void ws_fft_pass(float2* buf, const WsTwiddles<N, NX>
     if constexpr (!LAST) nbar_sync(kBarFft, NX);
 }
 
-template <int N, int RB, int NX, int RS, int PD, int P = 0, class OT, class F>
-__device__ __forceinline__ void ws_fft_rows(float2* buf, const WsTwiddles<N, NX>& tw, OT* __restrict__ Yb, int rows,
-                                            int lt, F&& after_last_read)
+template <int N, int RB, int NX, int RS, int PD, int RC = 16, int P = 0, class OT, class F>
+__device__ __forceinline__ void ws_fft_rows(float2* buf, const WsTwiddles<N, NX, RC>& tw, OT* __restrict__ Yb,
+                                            int rows, int lt, F&& after_last_read)
 {
-    if constexpr (P < fft_npass(N)) {
-        ws_fft_pass<N, RB, NX, RS, PD, P>(buf, tw, Yb, rows, lt, after_last_read);
-        ws_fft_rows<N, RB, NX, RS, PD, P + 1>(buf, tw, Yb, rows, lt, after_last_read);
+    if constexpr (P < fft_npass_r(N, RC, RC)) {
+        ws_fft_pass<N, RB, NX, RS, PD, RC, P>(buf, tw, Yb, rows, lt, after_last_read);
+        ws_fft_rows<N, RB, NX, RS, PD, RC, P + 1>(buf, tw, Yb, rows, lt, after_last_read);
     }
 }
 
@@ -417,7 +422,7 @@ __device__ __forceinline__ void ws_fft_role(const PpfWork& wl, float2* X, const 
 {
     constexpr int N = C::N, RB = C::RB, NX = C::NX;
     const int lt = threadIdx.x - C::NF;
-    WsTwiddles<N, NX> twr;
+    WsTwiddles<N, NX, C::RC> twr;
     twr.load(tw, lt);
     int gb = 0;
     for (int it = blockIdx.x;; it += gridDim.x) {
@@ -435,7 +440,7 @@ __device__ __forceinline__ void ws_fft_role(const PpfWork& wl, float2* X, const 
             nbar_sync(kBarFull0 + j, C::NT);
             const int64_t s0 = s_lo + (int64_t)b * RB;
             const int rows = (int)(s_hi - s0 < RB ? s_hi - s0 : RB);
-            ws_fft_rows<N, RB, NX, C::RS, C::PD>(X + j * C::BUF_SLOTS, twr, Y + s0 * N, rows, lt,
+            ws_fft_rows<N, RB, NX, C::RS, C::PD, C::RC>(X + j * C::BUF_SLOTS, twr, Y + s0 * N, rows, lt,
                                                  [&] { nbar_arrive(kBarEmpty0 + j, C::NT); });
         }
     }

@@ -22,6 +22,11 @@ static int variants_impl(int N, int T, int want, KernelEntry* out)
     PPF_WV(2048, 4, 256, 128, 2, 4, 2, 1)     PPF_WV(2048, 8, 256, 128, 1, 9, 2, 1)
     // N = 4096: FFT threads a multiple of 256 (fixed pass twiddles)
     PPF_WV(4096, 4, 256, 256, 1, 5, 2, 2) PPF_WV(4096, 4, 128, 256, 1, 5, 2, 2)
+    // radix-32 passes: N = 512 as 32 x 16, N = 1024 as 32 x 32
+    PPF_WV32(512, 4, 256, 128, 8, 4, 2) PPF_WV32(512, 8, 256, 128, 8, 4, 2)
+    PPF_WV32(512, 16, 256, 128, 8, 4, 2) PPF_WV32(512, 32, 256, 128, 4, 10, 2)
+    PPF_WV32(1024, 4, 256, 128, 4, 4, 2) PPF_WV32(1024, 8, 256, 128, 4, 4, 2)
+    PPF_WV32(1024, 16, 256, 64, 2, 10, 2)
     return idx;
 }
 

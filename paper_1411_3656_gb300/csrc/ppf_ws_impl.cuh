@@ -54,8 +54,8 @@ template <class C>
 KernelEntry entry()
 {
     static char name[64];
-    std::snprintf(name, sizeof(name), "ws:nf%d:nx%d:rb%d:nch%d%s%s%s", C::NF, C::NX, C::RB, C::NCH,
-                  C::CPT == 1 ? ":c1" : "", C::PD == 2 ? ":pd2" : "",
+    std::snprintf(name, sizeof(name), "ws:nf%d:nx%d:rb%d:nch%d%s%s%s%s", C::NF, C::NX, C::RB, C::NCH,
+                  C::CPT == 1 ? ":c1" : "", C::PD == 2 ? ":pd2" : "", C::RC == 32 ? ":r32" : "",
                   std::is_same<typename C::OT, BinF16>::value ? ":f16" : "");
     KernelEntry e;
     e.name = name;
@@ -78,6 +78,14 @@ KernelEntry entry()
         if (idx == want && out)                                                                      \
             *out = ws_detail::entry<WsCfg<NN, TT, In, NF, NX, RB, NCH, CPT, float2, PD>>();          \
         ++idx;                                                                                       \
+    }
+// PPF_WV32: the same with FFT passes of radix up to 32 (N = 512 or 1024 in two
+// passes).
+#define PPF_WV32(NN, TT, NF, NX, RB, NCH, CPT)                                                      \
+    if (N == NN && T == TT) {                                                                       \
+        if (idx == want && out)                                                                     \
+            *out = ws_detail::entry<WsCfg<NN, TT, In, NF, NX, RB, NCH, CPT, float2, 1, 32>>();      \
+        ++idx;                                                                                      \
     }
 // PPF_WVF: the FP16-output twin of a tile shape (complex64 input).
 #define PPF_WVF(NN, TT, NF, NX, RB, NCH, CPT, PD)                                                   \

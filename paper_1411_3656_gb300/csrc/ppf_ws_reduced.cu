@@ -33,6 +33,11 @@ static int variants_impl(int N, int T, int want, KernelEntry* out)
         // int8 rows (8 KiB at N = 4096) leave room for deeper blocks
         PPF_WV(2048, 8, 256, 128, 2, 10, 2, 2)
     }
+    // radix-32 passes: N = 512 as 32 x 16, N = 1024 as 32 x 32
+    PPF_WV32(512, 4, 256, 128, 8, 4, 2) PPF_WV32(512, 8, 256, 128, 8, 4, 2)
+    PPF_WV32(512, 16, 256, 128, 8, 4, 2) PPF_WV32(512, 32, 256, 128, 8, 6, 2)
+    PPF_WV32(1024, 4, 256, 128, 4, 4, 2) PPF_WV32(1024, 8, 256, 128, 4, 4, 2)
+    PPF_WV32(1024, 16, 256, 128, 4, 6, 2) PPF_WV32(1024, 32, 256, 64, 2, 18, 2)
     return idx;
 }
 
