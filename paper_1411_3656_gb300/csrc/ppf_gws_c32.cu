@@ -40,6 +40,7 @@ static int variants_f16_impl(int N, int T, int want, KernelEntry* out)
 {
     int idx = 0;
     PPF_GWVF(4096, 8, 4, 256, 256, 1, 4, 2, 1) PPF_GWVF(1024, 32, 2, 256, 256, 4, 6, 1, 1)
+    PPF_GWVRF(4096, 8, 4, 256, 256, 1, 4, 2, 1, 0, 0, 1) PPF_GWVRF(4096, 32, 8, 256, 256, 1, 6, 1, 1, 136, 120, 0)
     return idx;
 }
 

@@ -127,6 +127,13 @@ KernelEntry entry()
             *out = gws_detail::entry<GwsCfg<NN, TT, In, P, NF, NX, RB, NCH, NXB, float2, PD, RF, RX, ER>>(); \
         ++idx;                                                                                           \
     }
+// PPF_GWVRF: the FP16-output twin of a PPF_GWVR tile shape.
+#define PPF_GWVRF(NN, TT, P, NF, NX, RB, NCH, NXB, PD, RF, RX, ER)                                       \
+    if (N == NN && T == TT) {                                                                            \
+        if (idx == want && out)                                                                          \
+            *out = gws_detail::entry<GwsCfg<NN, TT, In, P, NF, NX, RB, NCH, NXB, BinF16, PD, RF, RX, ER>>(); \
+        ++idx;                                                                                           \
+    }
 #define PPF_GWVF(NN, TT, P, NF, NX, RB, NCH, NXB, PD)                                                    \
     if (N == NN && T == TT) {                                                                            \
         if (idx == want && out)                                                                          \

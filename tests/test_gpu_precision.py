@@ -69,15 +69,22 @@ def test_precision_report_n1024_t8(ppf, dtype):
     Y = Y.cpu().numpy()
     assert Y.shape == (S, N)
 
-    err_stored = synth.rel_l2(Y, oracle.ppf(xs, h, N, T, S))
+    ref_stored = oracle.ppf(xs, h, N, T, S)
     h_dev = h if dtype == "c32" else h.astype(np.float16).astype(np.float32)
-    err_device_h = synth.rel_l2(Y, oracle.ppf(xs, h_dev, N, T, S))
-    err_unrounded = synth.rel_l2(Y, oracle.ppf(x_orig, h, N, T, S))
+    ref_device_h = oracle.ppf(xs, h_dev, N, T, S)
+    ref_unrounded = oracle.ppf(x_orig, h, N, T, S)
+    err_stored = synth.rel_l2(Y, ref_stored)
+    err_device_h = synth.rel_l2(Y, ref_device_h)
+    err_unrounded = synth.rel_l2(Y, ref_unrounded)
+    # beside each whole-array error, the worst single spectrum's
     print("precision: " + json.dumps({
         "N": N, "T": T, "S": S, "input": dtype, "kernel": plan.kernel,
         "rel_l2_vs_oracle_on_stored_input": err_stored,
+        "worst_spectrum_on_stored_input": synth.worst_spectrum_rel_l2(Y, ref_stored),
         "rel_l2_vs_oracle_with_device_h": err_device_h,
-        "rel_l2_vs_oracle_on_unrounded_input": err_unrounded}))
+        "worst_spectrum_with_device_h": synth.worst_spectrum_rel_l2(Y, ref_device_h),
+        "rel_l2_vs_oracle_on_unrounded_input": err_unrounded,
+        "worst_spectrum_on_unrounded_input": synth.worst_spectrum_rel_l2(Y, ref_unrounded)}))
     plan.close()
 
     assert err_device_h <= 1e-5, err_device_h
