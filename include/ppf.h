@@ -380,6 +380,18 @@ int64_t ppf_launch_count(void);
 ppf_status_t ppf_check_timeout(unsigned limit_us, void* stream);
 
 /*
+ * ppf_fma_peak -- FP32 throughput probe for the roofline of FMA-bound tiles
+ * (no paper counterpart; measurement infrastructure).  Enqueues on `stream`
+ * (cudaStream_t as void*) one launch of `blocks` (1..65535) CTAs of 512
+ * threads, each thread running 8 independent chains of `iters` (1..2^24)
+ * packed FP32 FMAs (fma.rn.f32x2), and stores in *lane_fmas the number of
+ * scalar FMA lanes the launch executes; the caller times the launch (CUDA
+ * events on the same stream) and divides.  Reads and writes no memory.
+ * Errors: PPF_ERR_INVALID_ARG, PPF_ERR_CUDA (launch failure).
+ */
+ppf_status_t ppf_fma_peak(int blocks, int iters, void* stream, double* lane_fmas);
+
+/*
  * ppf_check_violations -- out-of-bounds accesses counted by the checked
  * build of this library (compiled with -DPPF_CHECKED: every instrumented
  * shared-memory and global access of the kernels first tests its index

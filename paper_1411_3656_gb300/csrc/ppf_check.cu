@@ -25,7 +25,38 @@ __global__ void wait_timeout_kernel(uint64_t limit_ns, int* err)
     if (__any_sync(0xffffffffu, !ok) && threadIdx.x == 0) atomicExch(err, 1);
 }
 
+// FP32 throughput probe: every thread runs kChains independent chains of
+// packed FMAs (a <- a * m + c on float2 lanes), so each issue has work that
+// does not wait on the one before; the result is written only if it matches
+// an impossible value, which keeps the chains alive without memory traffic.
+constexpr int kChains = 8;
+__global__ void __launch_bounds__(512) fma_peak_kernel(int iters, float2* sink)
+{
+    float2 a[kChains];
+#pragma unroll
+    for (int k = 0; k < kChains; ++k) a[k] = make_float2(1.0f + 1e-3f * threadIdx.x, 1.0f + 1e-3f * k);
+    const float2 m = make_float2(0.999999f, 1.000001f), c = make_float2(1e-7f, -1e-7f);
+    for (int i = 0; i < iters; ++i) {
+#pragma unroll
+        for (int k = 0; k < kChains; ++k) a[k] = __ffma2_rn(a[k], m, c);
+    }
+    float acc = 0.f;
+#pragma unroll
+    for (int k = 0; k < kChains; ++k) acc += a[k].x + a[k].y;
+    if (acc == -1.0f) sink[blockIdx.x * blockDim.x + threadIdx.x] = make_float2(acc, acc);
+}
+
 }  // namespace
+
+extern "C" ppf_status_t ppf_fma_peak(int blocks, int iters, void* stream, double* lane_fmas)
+{
+    if (blocks < 1 || blocks > 65535 || iters < 1 || iters > (1 << 24) || !lane_fmas) return PPF_ERR_INVALID_ARG;
+    fma_peak_kernel<<<blocks, 512, 0, static_cast<cudaStream_t>(stream)>>>(iters, nullptr);
+    ppf::note_launch();
+    if (cudaGetLastError() != cudaSuccess) return PPF_ERR_CUDA;
+    *lane_fmas = (double)blocks * 512.0 * (double)iters * kChains * 2.0;
+    return PPF_OK;
+}
 
 extern "C" ppf_status_t ppf_check_timeout(unsigned limit_us, void* stream)
 {

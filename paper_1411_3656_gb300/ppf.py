@@ -38,7 +38,7 @@ EXPORTS = ("ppf_plan_create", "ppf_plan_destroy", "ppf_execute", "ppf_execute_ho
            "ppf_batch_launches", "ppf_batch_destroy", "ppf_server_create", "ppf_server_admit",
            "ppf_server_release", "ppf_server_submit", "ppf_server_submit_many", "ppf_server_tick", "ppf_server_position",
            "ppf_server_info", "ppf_server_graph_ticks", "ppf_server_destroy", "ppf_design_coeffs", "ppf_check_timeout",
-           "ppf_check_violations")
+           "ppf_check_violations", "ppf_fma_peak")
 
 
 class PPFJob(ctypes.Structure):
@@ -108,6 +108,7 @@ def load(path: str | None = None):
             "ppf_design_coeffs": ([i32, i32, i32, ctypes.c_double, ctypes.POINTER(ctypes.c_float)], i32),
             "ppf_check_timeout": ([ctypes.c_uint, vp], i32),
             "ppf_check_violations": ([i32], i64),
+            "ppf_fma_peak": ([i32, i32, vp, ctypes.POINTER(ctypes.c_double)], i32),
         }
         for name, (args, res) in sig.items():
             fn = getattr(lib, name)
@@ -229,6 +230,13 @@ def ppf_execute_noalloc(N: int, T: int, dtype: str, d_h: int, d_in: int, d_out: 
 def ppf_check_timeout(limit_us: int = 1000, stream=None) -> int:
     """Run the device bounded-wait self-check; returns the status (PPF_ERR_TIMEOUT expected)."""
     return load().ppf_check_timeout(int(limit_us), _stream_ptr(stream))
+
+
+def ppf_fma_peak(blocks: int, iters: int, stream=None):
+    """Enqueue the FP32 packed-FMA probe; returns (status, scalar FMA lanes the launch executes)."""
+    n = ctypes.c_double(0.0)
+    st = load().ppf_fma_peak(int(blocks), int(iters), _stream_ptr(stream), ctypes.byref(n))
+    return st, n.value
 
 
 WINDOWS = {"hamming": 0, "kaiser": 1}

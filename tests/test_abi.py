@@ -89,3 +89,12 @@ def test_tuned_table_names_compiled_variants(lib):
         assert ppf.ppf_variant_name(N, T, dtypes[d], i) == name, ln
         n += 1
     assert n >= 3 * 20
+
+
+def test_fma_peak_argument_errors_without_a_device(lib):
+    """The FP32 probe refuses bad arguments before touching the device."""
+    from paper_1411_3656_gb300 import ppf
+    bad = {v: k for k, v in ppf.STATUS.items()}["PPF_ERR_INVALID_ARG"]
+    for blocks, iters in ((0, 10), (70000, 10), (4, 0), (4, 1 << 25)):
+        st, n = ppf.ppf_fma_peak(blocks, iters, 0)
+        assert st == bad, (blocks, iters, st)
