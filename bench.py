@@ -104,11 +104,15 @@ def peaks():
 
 
 def kernel_source_hash() -> str:
-    """sha256 over the CUDA sources and the tuned table (identifies a kernel build)."""
+    """sha256 over the CUDA sources and the tuned table (identifies a kernel
+    build); ppf_check.cu (the device self-checks and the FP32 probe, none of
+    them a PPF kernel) is left out."""
     import glob
     import hashlib
     hh = hashlib.sha256()
     for f in sorted(glob.glob(os.path.join(ROOT, "paper_1411_3656_gb300", "csrc", "*"))):
+        if os.path.basename(f) == "ppf_check.cu":
+            continue
         with open(f, "rb") as fh:
             hh.update(os.path.basename(f).encode() + fh.read())
     return hh.hexdigest()
