@@ -38,7 +38,7 @@
 namespace ppf {
 
 template <int N_, int T_, class In_, int P_, int NF_, int NX_, int RB_, int NCH_, int NXB_ = 1, class OT_ = float2,
-          int PD_ = 1, int RF_ = 0, int RX_ = 0, int ER_ = 0>
+          int PD_ = 1, int RF_ = 0, int RX_ = 0, int ER_ = 0, int PF_ = 0>
 struct GwsCfg {
     using OT = OT_;  // output bin: float2 (complex64) or BinF16
     using In = In_;
@@ -59,6 +59,10 @@ struct GwsCfg {
     // is refilled mid-round, at the cost of a second FIR barrier per round
     static constexpr bool EARLY = ER_ != 0 && RG == 1 && RBT + T - 1 > ROWS;
     static_assert(ER_ == 0 || EARLY, "early refill needs one row group and a window past its first chunk");
+    // L2 prefetch distance (PF > 0): when chunk k of an item is copied into
+    // the ring, chunk k + PF is prefetched into L2, so PF more chunks of the
+    // stream are in flight than the ring itself holds
+    static constexpr int PF = PF_;
     static constexpr int RING_ROWS = NCH * ROWS;
     static constexpr int SEG_BYTES = NC * BPS;           // one input row's slice
     static constexpr int CHUNK_BYTES = ROWS * SEG_BYTES;
@@ -160,6 +164,12 @@ __device__ __forceinline__ void gws_fir_role(const PpfWork& wl, unsigned char* r
         const int nchunks = (int)((in_end - s_lo + ROWS - 1) / ROWS);
 
         int issued = 0;  // chunks of this item issued so far (meaningful in thread 0)
+        // L2 prefetch of chunk k's rows (only rows the item reads)
+        auto prefetch = [&](int k) {
+            const int64_t r0 = s_lo + (int64_t)k * ROWS;
+            const int nrows = (int)(in_end - r0 < ROWS ? in_end - r0 : ROWS);
+            for (int q = 0; q < nrows; ++q) l2_prefetch_1d(x + (r0 + q) * N + rank * NC, (uint32_t)C::SEG_BYTES);
+        };
         auto issue = [&](int k) {
             const int64_t r0 = s_lo + (int64_t)k * ROWS;
             const int nrows = (int)(in_end - r0 < ROWS ? in_end - r0 : ROWS);
@@ -170,6 +180,10 @@ __device__ __forceinline__ void gws_fir_role(const PpfWork& wl, unsigned char* r
             for (int q = 0; q < (ok ? nrows : 0); ++q)
                 tma_load_1d(ring + slot * C::CHUNK_BYTES + q * C::SEG_BYTES, x + (r0 + q) * N + rank * NC,
                             (uint32_t)C::SEG_BYTES, &bars[slot], policy);
+            if constexpr (C::PF > 0) {
+                // (chunks of the ring's first fill are copied at once)
+                if (k + C::PF < nchunks && k + C::PF >= NCH) prefetch(k + C::PF);
+            }
         };
         if (tid == 0 && !failed) {
             const int first = nchunks < NCH ? nchunks : NCH;

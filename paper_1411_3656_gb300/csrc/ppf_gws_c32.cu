@@ -26,6 +26,13 @@ static int variants_impl(int N, int T, int want, KernelEntry* out)
     // early ring refill
     PPF_GWVR(4096, 8, 4, 256, 256, 1, 4, 2, 1, 0, 0, 1) PPF_GWVR(4096, 16, 8, 256, 256, 1, 4, 2, 1, 0, 0, 1)
     PPF_GWVR(2048, 16, 4, 256, 256, 2, 4, 2, 1, 0, 0, 1)
+    // chunks prefetched into L2 ahead of the ring copies
+    PPF_GWVP(4096, 32, 8, 256, 256, 1, 6, 1, 1, 136, 120, 0, 2) PPF_GWVP(4096, 32, 8, 256, 256, 1, 6, 1, 1, 136, 120, 0, 4)
+    PPF_GWVP(4096, 32, 8, 256, 256, 1, 6, 1, 1, 136, 120, 0, 8) PPF_GWVP(4096, 32, 8, 256, 256, 1, 5, 2, 2, 136, 120, 0, 4)
+    PPF_GWVP(4096, 32, 8, 256, 256, 1, 5, 2, 2, 136, 120, 1, 4)
+    PPF_GWVP(2048, 32, 4, 256, 256, 2, 6, 1, 1, 128, 128, 0, 4) PPF_GWVP(1024, 32, 2, 256, 256, 4, 6, 1, 1, 128, 128, 0, 4)
+    PPF_GWVP(4096, 8, 4, 256, 256, 1, 4, 2, 1, 0, 0, 1, 4) PPF_GWVP(4096, 16, 8, 256, 256, 1, 4, 2, 1, 0, 0, 0, 4)
+    PPF_GWVP(2048, 16, 4, 256, 256, 2, 4, 2, 1, 0, 0, 0, 4)
     return idx;
 }
 
@@ -41,6 +48,8 @@ static int variants_f16_impl(int N, int T, int want, KernelEntry* out)
     int idx = 0;
     PPF_GWVF(4096, 8, 4, 256, 256, 1, 4, 2, 1) PPF_GWVF(1024, 32, 2, 256, 256, 4, 6, 1, 1)
     PPF_GWVRF(4096, 8, 4, 256, 256, 1, 4, 2, 1, 0, 0, 1) PPF_GWVRF(4096, 32, 8, 256, 256, 1, 6, 1, 1, 136, 120, 0)
+    PPF_GWVPF(4096, 32, 8, 256, 256, 1, 6, 1, 1, 136, 120, 0, 4) PPF_GWVPF(1024, 32, 2, 256, 256, 4, 6, 1, 1, 128, 128, 0, 4)
+    PPF_GWVPF(4096, 8, 4, 256, 256, 1, 4, 2, 1, 0, 0, 1, 4)
     return idx;
 }
 

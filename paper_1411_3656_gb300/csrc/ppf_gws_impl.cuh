@@ -89,10 +89,11 @@ cudaError_t launch_gws_work(const PlanView& p, const PpfWork& w, int grid, cudaS
 template <class C>
 KernelEntry entry()
 {
-    static char name[96];
-    char split[24] = "";
+    static char name[112];
+    char split[40] = "";
     if (C::RF > 0) std::snprintf(split, sizeof(split), ":r%d/%d", C::RF, C::RX);
     if (C::EARLY) std::snprintf(split + std::strlen(split), sizeof(split) - std::strlen(split), ":er");
+    if (C::PF > 0) std::snprintf(split + std::strlen(split), sizeof(split) - std::strlen(split), ":pf%d", C::PF);
     std::snprintf(name, sizeof(name), "gws:p%d:nf%d:nx%d:rb%d:nch%d%s%s%s%s", C::P, C::NF, C::NX, C::RB, C::NCH,
                   C::NXB == 2 ? ":db" : "", C::PD == 2 ? ":pd2" : "", split,
                   std::is_same<typename C::OT, BinF16>::value ? ":f16" : "");
@@ -125,6 +126,20 @@ KernelEntry entry()
     if (N == NN && T == TT) {                                                                            \
         if (idx == want && out)                                                                          \
             *out = gws_detail::entry<GwsCfg<NN, TT, In, P, NF, NX, RB, NCH, NXB, float2, PD, RF, RX, ER>>(); \
+        ++idx;                                                                                           \
+    }
+// PPF_GWVP: a PPF_GWVR tile shape with chunks prefetched into L2 PF chunks
+// ahead of the ring copies; PPF_GWVPF its FP16-output twin.
+#define PPF_GWVP(NN, TT, P, NF, NX, RB, NCH, NXB, PD, RF, RX, ER, PF)                                    \
+    if (N == NN && T == TT) {                                                                            \
+        if (idx == want && out)                                                                          \
+            *out = gws_detail::entry<GwsCfg<NN, TT, In, P, NF, NX, RB, NCH, NXB, float2, PD, RF, RX, ER, PF>>(); \
+        ++idx;                                                                                           \
+    }
+#define PPF_GWVPF(NN, TT, P, NF, NX, RB, NCH, NXB, PD, RF, RX, ER, PF)                                   \
+    if (N == NN && T == TT) {                                                                            \
+        if (idx == want && out)                                                                          \
+            *out = gws_detail::entry<GwsCfg<NN, TT, In, P, NF, NX, RB, NCH, NXB, BinF16, PD, RF, RX, ER, PF>>(); \
         ++idx;                                                                                           \
     }
 // PPF_GWVRF: the FP16-output twin of a PPF_GWVR tile shape.

@@ -83,6 +83,15 @@ __device__ __forceinline__ void tma_load_1d(void* dst, const void* src, uint32_t
         : "memory");
 }
 
+// 1-D bulk prefetch global -> L2 (no completion, no shared memory): pulls a
+// ring chunk the CTA will copy later into L2 ahead of time, so that more of
+// the stream is in flight than the ring holds.  src 16-byte aligned, bytes a
+// multiple of 16, the whole range inside the caller's input buffer.
+__device__ __forceinline__ void l2_prefetch_1d(const void* src, uint32_t bytes)
+{
+    asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(src), "r"(bytes) : "memory");
+}
+
 // ---------------------------------------------------------------- clusters
 __device__ __forceinline__ uint32_t cluster_ctarank()
 {
