@@ -264,3 +264,146 @@ def test_warp_specialised_planted_mistakes_fail(mistake, nxb):
     with pytest.raises(AssertionError):
         for seed in range(30):
             run_gws_model(4, 8, nxb, 100 + seed, trials=20, **{mistake: True})
+
+
+# --------------------------------------------------------------------------
+# The ring of input chunks in the gather-type kernels: NCH shared-memory slots
+# of ROWS rows each, one mbarrier per slot (the copy of chunk c lands in slot
+# c mod NCH and completes phase c // NCH of its barrier).  A round k reads the
+# window of rows k*ROWS .. k*ROWS + ROWS + T - 2, i.e. chunks k .. k + KO.
+#   After the round (the normal form) every FIR thread has waited for all of
+#   them at the round's start; a barrier after the round's reads lets thread 0
+#   copy chunk k + NCH into the slot of chunk k.
+#   With the early refill (the ":er" tiles) a thread waits for chunk k + w
+#   right before its window reaches row w*ROWS, and the barrier sits right
+#   after the window's first ROWS rows, so the refill of chunk k's slot is
+#   issued mid-round.
+# Copies land after random delays.  The model checks that every row is read
+# from a slot holding the chunk it belongs to, after that chunk's copy landed,
+# that no parity wait sees its barrier two phases ahead, and that every
+# interleaving finishes; planting the barrier one row too early, or letting
+# thread 0 refill without the barrier, fails.
+
+
+class Ring:
+    def __init__(self, nch):
+        self.content = [None] * nch     # chunk whose copy has landed in the slot
+        self.pending = [None] * nch     # chunk whose copy is in flight into the slot
+        self.bars = [Barrier(1) for _ in range(nch)]
+
+
+def ring_programs(nthr, nch, rows, T, nr, early, rng, refill_row=None, no_barrier=False):
+    ko = (T - 2) // rows + 1 if T >= 2 else 0
+    window = rows + T - 1
+    nchunks = (nr * rows + T - 1 + rows - 1) // rows
+    refill_row = rows if refill_row is None else refill_row
+    ring = Ring(nch)
+    state = {"issued": 0, "arrived": [0] * (nr + 1), "inflight": []}
+
+    def issue(c):
+        s = c % nch
+        assert ring.pending[s] is None
+        ring.pending[s] = c
+        state["inflight"].append(s)
+
+    def copier():
+        # lands in-flight copies one at a time, in random order
+        while True:
+            if state["inflight"]:
+                s = state["inflight"].pop(rng.randrange(len(state["inflight"])))
+                ring.content[s] = ring.pending[s]
+                ring.pending[s] = None
+                ring.bars[s].arrive()
+            yield None
+
+    def wait_chunk(c):
+        s = c % nch
+        while not ring.bars[s].wait_ready(c // nch):
+            yield "wait"
+
+    def read_row(k, u):
+        c = k + u // rows
+        if c < nchunks:
+            assert ring.content[c % nch] == c, f"row of chunk {c} read from a slot holding {ring.content[c % nch]}"
+
+    def barrier(k, tid):
+        state["arrived"][k] += 1
+        while state["arrived"][k] < nthr:
+            yield "wait"
+
+    def refill(k, tid):
+        if not no_barrier:
+            yield from barrier(k, tid)
+        if tid == 0 and state["issued"] < nchunks and state["issued"] == k + nch:
+            issue(state["issued"])
+            state["issued"] += 1
+
+    def thread(tid):
+        if tid == 0:
+            first = min(nch, nchunks)
+            for c in range(first):
+                issue(c)
+            state["issued"] = first
+        waited = 0
+        for k in range(nr):
+            if not early:
+                need = min(k + ko, nchunks - 1) + 1
+                while waited < need:
+                    yield from wait_chunk(waited)
+                    waited += 1
+            for u in range(window):
+                if early:
+                    if u % rows == 0:
+                        need = min(k + u // rows, nchunks - 1) + 1
+                        while waited < need:
+                            yield from wait_chunk(waited)
+                            waited += 1
+                    if u == refill_row:
+                        yield from refill(k, tid)
+                read_row(k, u)
+                yield None
+            if not early:
+                yield from refill(k, tid)
+
+    return [thread(t) for t in range(nthr)], copier()
+
+
+def run_ring_model(nthr, nch, rows, T, nr, early, seed, trials=30, **mistake):
+    rng = random.Random(seed)
+    for trial in range(trials):
+        threads, copier = ring_programs(nthr, nch, rows, T, nr, early, rng, **mistake)
+        live = set(range(nthr))
+        steps = 0
+        while live:
+            steps += 1
+            assert steps < 400000, "ring model did not finish"
+            if rng.random() < 0.3:
+                next(copier)
+            t = rng.choice(sorted(live))
+            try:
+                next(threads[t])
+            except StopIteration:
+                live.discard(t)
+
+
+@pytest.mark.parametrize("early", [False, True])
+@pytest.mark.parametrize("nthr,nch,rows,T,nr,seed", [(3, 6, 8, 32, 9, 1), (2, 5, 8, 32, 6, 2), (3, 4, 4, 8, 11, 3),
+                                                     (4, 6, 2, 8, 7, 4), (2, 3, 4, 4, 9, 5)])
+def test_ring_refill_reads_only_landed_chunks(nthr, nch, rows, T, nr, early, seed):
+    run_ring_model(nthr, nch, rows, T, nr, early, seed)
+
+
+@pytest.mark.parametrize("mistake", [{"refill_row": 7}, {"no_barrier": True}])
+def test_early_refill_planted_mistakes_fail(mistake):
+    """The mid-round barrier placed one row before the window leaves its first
+    chunk, or thread 0 refilling without waiting for the others, is caught."""
+    with pytest.raises(AssertionError, match="read from a slot holding"):
+        for seed in range(30):
+            run_ring_model(3, 6, 8, 32, 9, True, 300 + seed, trials=20, **mistake)
+
+
+def test_ring_shorter_than_the_window_never_finishes():
+    """The kernels' static check (NCH >= KO + 1 chunks) is needed: with a ring
+    one chunk shorter than a round's window the model stalls."""
+    with pytest.raises(AssertionError, match="did not finish"):
+        run_ring_model(2, 4, 2, 8, 5, False, 7, trials=1)
