@@ -126,8 +126,11 @@ ppf_status_t ppf_execute(ppf_plan_t plan, const void* d_in, void* d_out,
 /*
  * ppf_execute_host -- the whole PPF on host buffers (the paper's single mode,
  * M_b, Section 3, Table 2): copies host->device, runs the fused kernel and
- * copies the spectra back, overlapping the copies of one slice with the
- * kernel of another.  Blocks until the result is in h_out.
+ * copies the spectra back, in slices of about 16 Mi samples through a
+ * three-stage pipeline (upload, kernel, download on their own streams, three
+ * staging slots), so the upload of one slice, the kernel of another and the
+ * download of a third run at the same time.  Blocks until the result is in
+ * h_out.
  *   h_in   host input, (n_spectra + T - 1) * N samples (pinned memory gives
  *          full link bandwidth; pageable memory works but is slower).
  *   h_out  host output, n_spectra * N complex64.

@@ -40,12 +40,18 @@ struct ppf_plan_s {
     void* d_h = nullptr;
     float2* d_tw = nullptr;
     int* h_err = nullptr;    // mapped host word a kernel sets when a bounded wait gives up
-    // staging for ppf_execute_host (allocated on first use)
+    // staging for ppf_execute_host (allocated on first use): kHostSlots
+    // slots of input and output, one stream per stage (upload, kernel,
+    // download) and per slot the events that hand a slice between stages
+    static constexpr int kHostSlots = 3;
     std::mutex host_mu;
-    void* d_stage_in[2] = {nullptr, nullptr};
-    float2* d_stage_out[2] = {nullptr, nullptr};
+    void* d_stage_in[kHostSlots] = {};
+    float2* d_stage_out[kHostSlots] = {};
     int64_t stage_rows = 0;  // spectra per slice the staging buffers hold
-    cudaStream_t copy_st[2] = {nullptr, nullptr};
+    cudaStream_t copy_st[3] = {};               // upload, kernel, download
+    cudaEvent_t ev_in[kHostSlots] = {};         // slice uploaded into the slot
+    cudaEvent_t ev_k[kHostSlots] = {};          // slot's slice transformed (input slot free)
+    cudaEvent_t ev_out[kHostSlots] = {};        // slot's spectra downloaded (output slot free)
 };
 
 struct ppf_stream_s {
@@ -125,11 +131,15 @@ void free_plan_memory(ppf_plan_s* p)
     if (p->d_h) cudaFree(p->d_h);
     if (p->d_tw) cudaFree(p->d_tw);
     if (p->h_err) cudaFreeHost(p->h_err);
-    for (int i = 0; i < 2; ++i) {
+    for (int i = 0; i < ppf_plan_s::kHostSlots; ++i) {
         if (p->d_stage_in[i]) cudaFree(p->d_stage_in[i]);
         if (p->d_stage_out[i]) cudaFree(p->d_stage_out[i]);
-        if (p->copy_st[i]) cudaStreamDestroy(p->copy_st[i]);
+        if (p->ev_in[i]) cudaEventDestroy(p->ev_in[i]);
+        if (p->ev_k[i]) cudaEventDestroy(p->ev_k[i]);
+        if (p->ev_out[i]) cudaEventDestroy(p->ev_out[i]);
     }
+    for (int i = 0; i < 3; ++i)
+        if (p->copy_st[i]) cudaStreamDestroy(p->copy_st[i]);
 }
 
 }  // namespace
@@ -298,50 +308,73 @@ ppf_status_t ppf_execute_host(ppf_plan_t plan, const void* h_in, void* h_out, in
     const PlanView& v = plan->view;
     const int bps = sample_bytes(plan->dtype);
     const int64_t N = v.N, T = v.T;
-    // Slices of about 32 Mi samples keep two slices in flight while the copy
-    // engines stream the neighbours (the paper's single mode, M_b).
-    int64_t rows = (int64_t)((32ll << 20) / N);
+    // Slices of about 16 Mi samples (shorter pipeline fill and drain per call
+    // than 32 Mi, measured faster over the 20-cell sweep) in a three-stage
+    // pipeline: the upload
+    // stream copies slice s into slot s mod 3 once the kernel of slice s - 3
+    // has read that slot, the kernel stream transforms it once it has landed
+    // and the download of slice s - 3 has emptied the output slot, and the
+    // download stream copies the spectra back; uploads and downloads of
+    // different slices run at the same time (the link is full duplex).
+    constexpr int NS = ppf_plan_s::kHostSlots;
+    int64_t rows = (int64_t)((16ll << 20) / N);
     if (rows < 1) rows = 1;
     cudaError_t e = cudaSuccess;
     if (plan->stage_rows < rows) {
-        for (int i = 0; i < 2; ++i) {
+        for (int i = 0; i < NS; ++i) {
             if (plan->d_stage_in[i]) cudaFree(plan->d_stage_in[i]);
             if (plan->d_stage_out[i]) cudaFree(plan->d_stage_out[i]);
             plan->d_stage_in[i] = nullptr;
             plan->d_stage_out[i] = nullptr;
         }
         plan->stage_rows = 0;
-        for (int i = 0; i < 2 && e == cudaSuccess; ++i) {
+        for (int i = 0; i < NS && e == cudaSuccess; ++i) {
             e = cudaMalloc(&plan->d_stage_in[i], (size_t)(rows + T - 1) * N * bps);
             if (e == cudaSuccess) e = cudaMalloc((void**)&plan->d_stage_out[i], (size_t)rows * N * sizeof(float2));
-            if (e == cudaSuccess && !plan->copy_st[i])
-                e = cudaStreamCreateWithFlags(&plan->copy_st[i], cudaStreamNonBlocking);
+            if (e == cudaSuccess && !plan->ev_in[i]) e = cudaEventCreateWithFlags(&plan->ev_in[i], cudaEventDisableTiming);
+            if (e == cudaSuccess && !plan->ev_k[i]) e = cudaEventCreateWithFlags(&plan->ev_k[i], cudaEventDisableTiming);
+            if (e == cudaSuccess && !plan->ev_out[i])
+                e = cudaEventCreateWithFlags(&plan->ev_out[i], cudaEventDisableTiming);
         }
+        for (int i = 0; i < 3 && e == cudaSuccess; ++i)
+            if (!plan->copy_st[i]) e = cudaStreamCreateWithFlags(&plan->copy_st[i], cudaStreamNonBlocking);
         if (e != cudaSuccess) return from_cuda(e);
         plan->stage_rows = rows;
     }
     cudaStream_t user = static_cast<cudaStream_t>(stream);
+    cudaStream_t up = plan->copy_st[0], kst = plan->copy_st[1], down = plan->copy_st[2];
     cudaEvent_t start_ev;
     e = cudaEventCreateWithFlags(&start_ev, cudaEventDisableTiming);
     if (e != cudaSuccess) return from_cuda(e);
     // Work already queued on the caller's stream comes first.
     e = cudaEventRecord(start_ev, user);
-    for (int i = 0; i < 2 && e == cudaSuccess; ++i) e = cudaStreamWaitEvent(plan->copy_st[i], start_ev, 0);
+    for (int i = 0; i < 3 && e == cudaSuccess; ++i) e = cudaStreamWaitEvent(plan->copy_st[i], start_ev, 0);
     const char* src = static_cast<const char*>(h_in);
     char* dst = static_cast<char*>(h_out);
-    int slice = 0;
+    int64_t slice = 0;
     for (int64_t s0 = 0; s0 < n_spectra && e == cudaSuccess; s0 += rows, ++slice) {
-        const int k = slice & 1;
+        const int k = (int)(slice % NS);
+        const bool reuse = slice >= NS;
         const int64_t n = n_spectra - s0 < rows ? n_spectra - s0 : rows;
-        cudaStream_t st = plan->copy_st[k];
-        e = cudaMemcpyAsync(plan->d_stage_in[k], src + (size_t)s0 * N * bps, (size_t)(n + T - 1) * N * bps,
-                            cudaMemcpyHostToDevice, st);
-        if (e == cudaSuccess) e = plan->entry.launch(v, plan->d_stage_in[k], plan->d_stage_out[k], n, st);
+        // upload: the slot's previous slice has been read by its kernel
+        if (reuse) e = cudaStreamWaitEvent(up, plan->ev_k[k], 0);
+        if (e == cudaSuccess)
+            e = cudaMemcpyAsync(plan->d_stage_in[k], src + (size_t)s0 * N * bps, (size_t)(n + T - 1) * N * bps,
+                                cudaMemcpyHostToDevice, up);
+        if (e == cudaSuccess) e = cudaEventRecord(plan->ev_in[k], up);
+        // kernel: the slice has landed and the slot's previous spectra are downloaded
+        if (e == cudaSuccess) e = cudaStreamWaitEvent(kst, plan->ev_in[k], 0);
+        if (e == cudaSuccess && reuse) e = cudaStreamWaitEvent(kst, plan->ev_out[k], 0);
+        if (e == cudaSuccess) e = plan->entry.launch(v, plan->d_stage_in[k], plan->d_stage_out[k], n, kst);
+        if (e == cudaSuccess) e = cudaEventRecord(plan->ev_k[k], kst);
+        // download
+        if (e == cudaSuccess) e = cudaStreamWaitEvent(down, plan->ev_k[k], 0);
         if (e == cudaSuccess)
             e = cudaMemcpyAsync(dst + (size_t)s0 * N * sizeof(float2), plan->d_stage_out[k],
-                                (size_t)n * N * sizeof(float2), cudaMemcpyDeviceToHost, st);
+                                (size_t)n * N * sizeof(float2), cudaMemcpyDeviceToHost, down);
+        if (e == cudaSuccess) e = cudaEventRecord(plan->ev_out[k], down);
     }
-    for (int i = 0; i < 2; ++i) {
+    for (int i = 0; i < 3; ++i) {
         cudaError_t e2 = cudaStreamSynchronize(plan->copy_st[i]);
         if (e == cudaSuccess) e = e2;
     }
