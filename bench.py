@@ -348,6 +348,34 @@ def job_msamples_per_s(samples_per_step_per_rank: int, steps: int, world: int, e
     return samples_per_step_per_rank * steps * world / (elapsed_ms / 1e3) / 1e6
 
 
+def link_peak(torch, xh, yh, dev, nbytes=1 << 30):
+    """GB/s of pinned host<->device copies in both directions at once (best of
+    3, 1 GiB each way), or None."""
+    try:
+        a = xh.reshape(-1).view(torch.uint8)
+        b = yh.reshape(-1).view(torch.uint8)
+        n = min(nbytes, a.numel(), b.numel())
+        a, b = a[:n], b[:n]
+        da = torch.empty(n, dtype=torch.uint8, device=dev)
+        db = torch.empty(n, dtype=torch.uint8, device=dev)
+        s1, s2 = torch.cuda.Stream(dev), torch.cuda.Stream(dev)
+        best = None
+        for _ in range(3):
+            torch.cuda.synchronize(dev)
+            t0 = time.perf_counter()
+            with torch.cuda.stream(s1):
+                da.copy_(a, non_blocking=True)
+            with torch.cuda.stream(s2):
+                b.copy_(db, non_blocking=True)
+            torch.cuda.synchronize(dev)
+            rate = 2 * n / (time.perf_counter() - t0) / 1e9
+            best = rate if best is None else max(best, rate)
+        del da, db
+        return best
+    except Exception:
+        return None
+
+
 def measured_fma_peak(ppf, torch, stream, n_sm):
     """FP32 TFLOP/s of the packed-FMA probe (2 flop per FMA lane), best of 5
     launches after 2 warm-up launches; None if the probe fails."""
@@ -673,6 +701,14 @@ def run_ours(args):
                "h2d_bytes_per_step": sum((S + T - 1) * N * bps for N, T, S, _ in plans),
                "d2h_bytes_per_step": sum(S * N * 8 for N, T, S, _ in plans),
                "steps": e_steps, "x_realtime": data_s * e_steps / e_el, "api": "ppf_execute_host"}
+        # the host link's own rate on this machine: pinned copies both ways at once
+        # (copy engines, no PPF work), the ceiling of the host-buffer path
+        link = link_peak(torch, xh, yh, dev)
+        if link:
+            moved = (e2e["h2d_bytes_per_step"] + e2e["d2h_bytes_per_step"]) * e_steps / e_el / 1e9
+            e2e.update({"link_GBs": round(moved, 1), "link_peak_GBs": round(link, 1),
+                        "frac_of_link": round(moved / link, 3),
+                        "link_peak_source": "pinned copies host->device and device->host at once, best of 3"})
         del xh, yh
 
     unfused = None
