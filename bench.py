@@ -371,6 +371,7 @@ def link_peak(torch, xh, yh, dev, nbytes=1 << 30):
             rate = 2 * n / (time.perf_counter() - t0) / 1e9
             best = rate if best is None else max(best, rate)
         del da, db
+        torch.cuda.empty_cache()
         return best
     except Exception:
         return None
